@@ -1,0 +1,23 @@
+"""CPU oracle for the Clenshaw-Curtis spherical-harmonic transform.
+
+TEST INFRASTRUCTURE.  This package is a plain, slow, obviously correct CPU
+restatement of Hotta & Ujiie (2018), "A nestable, multigrid-friendly grid on
+a sphere for global spectral models based on Clenshaw-Curtis quadrature".
+Only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it.  The GPU library
+never imports, links or calls anything here, and nothing here imports the
+GPU library: the two share no code.
+
+Contents (all FP64 except the binary128 Legendre recurrence of Sec. 4.1):
+
+* ``cc_nodes``, ``cc_weights``     -- Eq. (cc-points), Eq. (cc-wgt)
+* ``gauss_nodes_weights``          -- Eq. (gauss-quad)/(gauss-wgt) by the
+                                      Golub-Welsch eigenproblem
+* ``pnm_cc``, ``pnm_at``           -- P~_n^m by the recurrence in binary128
+* ``dft_forward``, ``dft_inverse`` -- Eq. (dFT) discretised, and its inverse
+* ``analysis``, ``synthesis``      -- Eq. (dSHT)/(cc-quad), Eq. (iSHT)/(iLT)
+* ``adjoint_analysis``, ``adjoint_synthesis`` -- transposes of the two
+* ``restrict_nested``              -- Sec. 3.2 / Appendix C
+"""
+from .cc_oracle import *  # noqa: F401,F403
+from .cc_oracle import __all__  # noqa: F401

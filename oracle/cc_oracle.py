@@ -1,0 +1,361 @@
+"""Plain FP64 oracle of the Clenshaw-Curtis spherical-harmonic transform.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Every function is
+the plain definition from the paper, with library primitives (matrix
+products, a symmetric eigensolver) as single steps and no blocking,
+folding or reordering of the sums.
+
+Conventions (readings of points the paper leaves open):
+
+* Nodes: theta_j = j pi/(J+1), j = 1..J, j = 1 northernmost; mu = sin(phi)
+  = cos(theta) (Eq. cc-points).
+* Spectra: complex array ``[ncoef][F]``; coefficient (m, n), 0 <= m <= n <= N,
+  is row ``m (N+1) - m (m-1)/2 + (n - m)``.  Only m >= 0 is stored; a real
+  field has X_n^{-m} = conj(X_n^m), so the synthesis (Eq. iSHT) reads
+  X = sum_n Re(X_n^0) P~_n^0 + 2 Re sum_{m>=1} sum_n X_n^m P~_n^m e^{i m lambda}.
+  The imaginary part of the m = 0 coefficients is ignored on input and is
+  exactly zero on output.
+* The inverse zonal DFT carries the zonal wavenumber m in its exponent (the
+  printed formula below Eq. iLT drops it); the forward DFT carries 1/I (the
+  discretised Eq. dFT), the inverse carries no factor.
+* No Condon-Shortley phase.
+* Adjoints are taken for the plain inner products: sum over grid points of
+  x y, and sum over stored coefficients of Re(conj(a) b).
+"""
+import ctypes
+
+import numpy as np
+
+from . import build_oracle
+
+__all__ = [
+    "ncoef", "coef_offset", "cc_nodes", "cc_weights", "gauss_nodes_weights",
+    "pnm_cc", "pnm_at", "dft_forward", "dft_inverse", "analysis",
+    "synthesis", "adjoint_analysis", "adjoint_synthesis", "restrict_nested",
+    "analysis_gauss", "synthesis_gauss", "legendre_forward_m",
+    "legendre_inverse_m", "nested_rows",
+]
+
+_lib = None
+
+
+def _clib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.oracle_pnm_cc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ip, ctypes.c_int, dp]
+        lib.oracle_pnm_at.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      dp, dp, ctypes.c_int, dp]
+        lib.oracle_cc_node_q.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
+        _lib = lib
+    return _lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------
+# Indexing of the packed triangular spectrum
+# --------------------------------------------------------------------------
+def ncoef(N):
+    """Number of stored coefficients (m >= 0) of a triangular truncation N."""
+    return (N + 1) * (N + 2) // 2
+
+
+def coef_offset(N, m):
+    """Row of coefficient (m, n = m) in the packed m-major layout."""
+    return m * (N + 1) - m * (m - 1) // 2
+
+
+# --------------------------------------------------------------------------
+# Quadrature: nodes and weights
+# --------------------------------------------------------------------------
+def cc_nodes(J):
+    """Clenshaw-Curtis (Fejer second rule) nodes, Eq. (cc-points).
+
+    Returns (theta, mu, sin_theta) for j = 1..J, theta_j = j pi/(J+1),
+    mu_j = cos(theta_j) = sin(phi_j)."""
+    j = np.arange(1, J + 1, dtype=np.float64)
+    theta = np.pi * j / (J + 1)
+    return theta, np.cos(theta), np.sin(theta)
+
+
+def cc_weights(J):
+    """Clenshaw-Curtis weights by the explicit sum of Eq. (cc-wgt).
+
+    w_j = 4 sin(theta_j)/(J+1) * sum_{p odd, 1<=p<=J} sin(p theta_j)/p,
+    with each sin(p theta_j) evaluated directly after reducing the integer
+    p*j modulo 2(J+1)."""
+    j = np.arange(1, J + 1, dtype=np.int64)[:, None]
+    p = np.arange(1, J + 1, 2, dtype=np.int64)[None, :]
+    r = (p * j) % (2 * (J + 1))
+    s = np.sin(np.pi * r / (J + 1))
+    sin_t = np.sin(np.pi * j[:, 0] / (J + 1))
+    return 4.0 * sin_t / (J + 1) * (s / p).sum(axis=1)
+
+
+def gauss_nodes_weights(J):
+    """Gauss-Legendre nodes and weights (Eq. gauss-quad/gauss-wgt).
+
+    Golub-Welsch: the nodes are the eigenvalues of the symmetric Jacobi
+    matrix of the Legendre three-term recurrence (off-diagonal
+    k/sqrt(4k^2-1)), the weights are 2 times the squared first components
+    of the normalised eigenvectors.  Ordered north to south (mu
+    decreasing).  Returns (mu, sin_theta, w)."""
+    k = np.arange(1, J, dtype=np.float64)
+    beta = k / np.sqrt(4.0 * k * k - 1.0)
+    T = np.diag(beta, 1) + np.diag(beta, -1)
+    x, V = np.linalg.eigh(T)
+    w = 2.0 * V[0, :] ** 2
+    order = np.argsort(-x)
+    x, w = x[order], w[order]
+    return x, np.sqrt((1.0 - x) * (1.0 + x)), w
+
+
+# --------------------------------------------------------------------------
+# Normalised associated Legendre functions (binary128 recurrence)
+# --------------------------------------------------------------------------
+def pnm_cc(N, J, m_lo=0, m_hi=None, j=None):
+    """P~_n^m(mu_j) at Clenshaw-Curtis nodes, from the binary128 recurrence.
+
+    Rows are (m, n) for m_lo <= m <= m_hi, n = m..N, packed m-major; columns
+    are the 1-based node indices ``j`` (default all 1..J)."""
+    if m_hi is None:
+        m_hi = N
+    jl = np.arange(1, J + 1, dtype=np.int32) if j is None else \
+        np.ascontiguousarray(j, dtype=np.int32)
+    rows = sum(N - m + 1 for m in range(m_lo, m_hi + 1))
+    out = np.empty((rows, len(jl)), dtype=np.float64)
+    rc = _clib().oracle_pnm_cc(N, J, m_lo, m_hi,
+                               jl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               len(jl), _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle_pnm_cc: bad arguments")
+    return out
+
+
+def pnm_at(N, cos_t, sin_t, m_lo=0, m_hi=None):
+    """P~_n^m at arbitrary points (FP64 cos/sin of colatitude)."""
+    if m_hi is None:
+        m_hi = N
+    c = np.ascontiguousarray(cos_t, dtype=np.float64)
+    s = np.ascontiguousarray(sin_t, dtype=np.float64)
+    rows = sum(N - m + 1 for m in range(m_lo, m_hi + 1))
+    out = np.empty((rows, len(c)), dtype=np.float64)
+    rc = _clib().oracle_pnm_at(N, m_lo, m_hi, _dptr(c), _dptr(s), len(c),
+                               _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle_pnm_at: bad arguments")
+    return out
+
+
+def cc_node_binary128(J, j):
+    """(cos, sin) of theta_j from the binary128 series, rounded to FP64."""
+    c = ctypes.c_double()
+    s = ctypes.c_double()
+    _clib().oracle_cc_node_q(J, j, ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+# --------------------------------------------------------------------------
+# Zonal Fourier transform (direct DFT)
+# --------------------------------------------------------------------------
+def _twiddle(I, ms, sign):
+    """exp(sign * 2 pi i * (m*i mod I)/I) as an [I][len(ms)] matrix."""
+    i = np.arange(I, dtype=np.int64)[:, None]
+    r = (np.asarray(ms, dtype=np.int64)[None, :] * i) % I
+    ang = 2.0 * np.pi * r / I
+    return np.cos(ang) + sign * 1j * np.sin(ang)
+
+
+def dft_forward(x, N, ms=None):
+    """X^m(phi_j) = (1/I) sum_i X(lambda_i, phi_j) e^{-i m lambda_i}.
+
+    Discretised Eq. (dFT) with lambda_i = 2 pi i/I; x is real [..., I];
+    returns complex [..., len(ms)] for m in ``ms`` (default 0..N)."""
+    I = x.shape[-1]
+    ms = np.arange(N + 1) if ms is None else ms
+    return (x @ _twiddle(I, ms, -1.0)) / I
+
+
+def dft_inverse(X, I, ms=None):
+    """Real field from zonal coefficients m >= 0 (conjugate symmetry).
+
+    x_i = Re(X^0) + 2 Re sum_{m>=1} X^m e^{+i m lambda_i}."""
+    M = X.shape[-1]
+    ms = np.arange(M) if ms is None else np.asarray(ms)
+    E = _twiddle(I, ms, +1.0).T                       # [len(ms)][I]
+    c = np.where(ms == 0, 1.0, 2.0)[:, None]
+    Xr = np.where(ms == 0, X.real + 0j, X)
+    return np.real(Xr @ (c * E))
+
+
+# --------------------------------------------------------------------------
+# Legendre transform for one zonal wavenumber
+# --------------------------------------------------------------------------
+def legendre_forward_m(Xm, P, w):
+    """X_n^m = sum_j X^m(phi_j) P~_n^m(mu_j) w_j (Eq. cc-quad / gauss-quad).
+
+    Xm: complex [F][J]; P: [rows][J]; w: [J].  Returns [rows][F]."""
+    return (P * w[None, :]) @ Xm.T
+
+
+def legendre_inverse_m(a, P):
+    """X^m(phi_j) = sum_n X_n^m P~_n^m(mu_j) (Eq. iLT).  a: [rows][F]."""
+    return (P.T @ a).T                                 # [F][J]
+
+
+# --------------------------------------------------------------------------
+# Full transforms
+# --------------------------------------------------------------------------
+def _analysis_general(x, N, pfun, w, ms=None):
+    F, J, I = x.shape
+    ms = range(N + 1) if ms is None else ms
+    X = dft_forward(x, N, ms=list(ms))                 # [F][J][len(ms)]
+    out = {}
+    for k, m in enumerate(ms):
+        P = pfun(m)
+        a = legendre_forward_m(X[:, :, k], P, w)
+        if m == 0:
+            a = a.real + 0j
+        out[m] = a
+    return out
+
+
+def analysis(x, N, ms=None):
+    """Forward SHT on the Clenshaw-Curtis grid, Eq. (dSHT) with the zonal
+    DFT and Eq. (cc-quad).  x: real [F][J][I] (j = 1 first).
+
+    Returns the packed spectrum [ncoef][F] (complex), or, if ``ms`` is given,
+    a dict m -> [N-m+1][F] for those zonal wavenumbers only."""
+    x = np.asarray(x, dtype=np.float64)
+    F, J, I = x.shape
+    w = cc_weights(J)
+    d = _analysis_general(x, N, lambda m: pnm_cc(N, J, m, m), w, ms)
+    if ms is not None:
+        return d
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m, a in d.items():
+        spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
+    return spec
+
+
+def _synthesis_general(spec, N, J, I, pfun, ms=None):
+    F = spec.shape[1]
+    ms = list(range(N + 1)) if ms is None else list(ms)
+    X = np.zeros((F, J, len(ms)), dtype=np.complex128)
+    for k, m in enumerate(ms):
+        a = spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
+        X[:, :, k] = legendre_inverse_m(a, pfun(m))
+    return dft_inverse(X, I, ms=ms)
+
+
+def synthesis(spec, N, J, I):
+    """Inverse SHT, Eq. (iSHT) via Eq. (iLT) and the inverse zonal DFT.
+
+    spec: complex [ncoef][F]; returns real [F][J][I]."""
+    spec = np.asarray(spec, dtype=np.complex128)
+    return _synthesis_general(spec, N, J, I, lambda m: pnm_cc(N, J, m, m))
+
+
+def analysis_gauss(x, N):
+    """Forward SHT on a Gaussian grid (Eq. gauss-quad), J = x.shape[1]."""
+    F, J, I = x.shape
+    mu, s, w = gauss_nodes_weights(J)
+    d = _analysis_general(np.asarray(x, np.float64), N,
+                          lambda m: pnm_at(N, mu, s, m, m), w)
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m, a in d.items():
+        spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
+    return spec
+
+
+def synthesis_gauss(spec, N, J, I):
+    """Inverse SHT evaluated on the J-point Gaussian grid."""
+    mu, s, _ = gauss_nodes_weights(J)
+    return _synthesis_general(np.asarray(spec, np.complex128), N, J, I,
+                              lambda m: pnm_at(N, mu, s, m, m))
+
+
+def adjoint_analysis(abar, N, J, I):
+    """Transpose of ``analysis`` (spectrum -> grid).
+
+    x~_ij = (w_j / I) sum_{m>=0} sum_n P~_n^m(mu_j) Re(a~_n^m e^{i m lambda_i}),
+    with no factor 2 for m >= 1 (the m = 0 imaginary part drops out)."""
+    abar = np.asarray(abar, dtype=np.complex128)
+    F = abar.shape[1]
+    w = cc_weights(J)
+    X = np.zeros((F, J, N + 1), dtype=np.complex128)
+    for m in range(N + 1):
+        a = abar[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
+        X[:, :, m] = legendre_inverse_m(a, pnm_cc(N, J, m, m))
+    E = _twiddle(I, np.arange(N + 1), +1.0).T           # [N+1][I]
+    return np.real(X @ E) * (w[None, :, None] / I)
+
+
+def adjoint_synthesis(xbar, N):
+    """Transpose of ``synthesis`` (grid -> spectrum).
+
+    a~_n^m = c_m sum_j P~_n^m(mu_j) sum_i x~_ij e^{-i m lambda_i}, c_0 = 1,
+    c_m = 2 (m >= 1); the m = 0 imaginary part is zero."""
+    xbar = np.asarray(xbar, dtype=np.float64)
+    F, J, I = xbar.shape
+    X = dft_forward(xbar, N) * I                      # no 1/I
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m in range(N + 1):
+        P = pnm_cc(N, J, m, m)
+        a = (2.0 if m >= 1 else 1.0) * (P @ X[:, :, m].T)
+        if m == 0:
+            a = a.real + 0j
+        spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
+    return spec
+
+
+# --------------------------------------------------------------------------
+# Nested grids (Sec. 3.2) and restriction (Appendix C)
+# --------------------------------------------------------------------------
+def nested_rows(J_c, k):
+    """1-based fine-grid latitude indices of the coarse nodes.
+
+    The J_c-point grid is nested in the J_f = 2^k (J_c+1) - 1 point grid:
+    theta^c_j = j pi/(J_c+1) = (2^k j) pi/(J_f+1)."""
+    return (2 ** k) * np.arange(1, J_c + 1)
+
+
+def restrict_nested(x_fine, k, N_c):
+    """Coarse spectrum from a fine grid by injection + coarse analysis.
+
+    The fine grid must have J_f = 2^k (J_c+1) - 1 latitudes and
+    I_f = 2^k I_c longitudes; the coarse grid is every 2^k-th latitude
+    starting at j = 2^k and every 2^k-th longitude starting at lambda = 0.
+    Returns the coarse CC analysis (truncation N_c) of that sub-grid."""
+    x_fine = np.asarray(x_fine, dtype=np.float64)
+    F, J_f, I_f = x_fine.shape
+    s = 2 ** k
+    if (J_f + 1) % s != 0 or I_f % s != 0:
+        raise ValueError("grid does not nest at this level")
+    J_c = (J_f + 1) // s - 1
+    rows = nested_rows(J_c, k) - 1
+    sub = x_fine[:, rows, ::s]
+    return analysis(sub, N_c)
+
+
+def orthonormality_errors(N, J, m, pnm=None, w=None):
+    """Normality and orthogonality errors of Eq. (norm-err)/(orth-err) for
+    zonal wavenumber m on the J-point Clenshaw-Curtis grid.  Returns two
+    arrays over n = m..N."""
+    P = pnm_cc(N, J, m, m) if pnm is None else pnm
+    w = cc_weights(J) if w is None else w
+    G = (P * w[None, :]) @ P.T
+    eN = np.abs(np.diag(G) - 1.0)
+    off = np.abs(G - np.diag(np.diag(G)))
+    eO = off.max(axis=1) if G.shape[0] > 1 else np.zeros(1)
+    return eN, eO
+
+
+__all__ += ["orthonormality_errors", "cc_node_binary128"]
