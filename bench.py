@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Throughput of the Clenshaw-Curtis spherical-harmonic transform on GB300.
+
+One step = one transform pair (synthesis then analysis) of every
+field-level of the workload (default T639: N=639, J=1281, I=2560, 256
+field-levels) with inputs resident in HBM.  ``value`` is field-level
+transform pairs per second over all ranks.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank transforms its own
+batch of field-levels (independent columns, no collective on the data
+path), timing is the max over ranks ("weak" scaling).  ``--impl reference``
+times the CPU oracle on the host cores instead (rank 0 only).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "T639 transform pairs/s per field-level"
+UNIT = "field-level transform pairs/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", default="T639")
+    ap.add_argument("--precision", default="auto",
+                    help="auto (headline path), fp64, bf16x3, ...")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch (explained in the design doc)
+# ---------------------------------------------------------------------------
+def legendre_flops(w, F):
+    """Folded contraction: 2 flops per (coefficient, northern node, real column)."""
+    ncoef = (w.N + 1) * (w.N + 2) // 2
+    Jh = (w.J + 1) // 2
+    return 2.0 * ncoef * Jh * 2 * F
+
+
+def fft_bytes(w, F, real_bytes):
+    """Grid read (or written) once + Fourier workspace written (or read) once."""
+    Jh = (w.J + 1) // 2
+    return F * w.J * w.I * real_bytes + (w.N + 1) * 2 * Jh * F * 2 * real_bytes
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+            "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(w, mstep):
+    """One field-level pair (synthesis then analysis) restricted to the zonal
+    wavenumbers m = 0, mstep, 2 mstep, ...; returns (seconds, fraction of the
+    full pair's Legendre work this sample covers)."""
+    import oracle as O
+    from paper_1711_11296_gb300 import workloads as W
+    a = W.workload_spectrum(w, F=1)
+    ms = list(range(0, w.N + 1, mstep))
+    ncoef = (w.N + 1) * (w.N + 2) // 2
+    frac = sum(w.N - m + 1 for m in ms) / ncoef
+    spec = np.zeros_like(a)
+    for m in ms:
+        r0 = O.coef_offset(w.N, m)
+        spec[r0:r0 + w.N - m + 1] = a[r0:r0 + w.N - m + 1]
+    t0 = time.perf_counter()
+    X = np.zeros((1, w.J, len(ms)), dtype=np.complex128)
+    for k, m in enumerate(ms):
+        r0 = O.coef_offset(w.N, m)
+        X[:, :, k] = O.legendre_inverse_m(spec[r0:r0 + w.N - m + 1],
+                                          O.pnm_cc(w.N, w.J, m, m))
+    grid = O.dft_inverse(X, w.I, ms=ms)
+    O.analysis(grid, w.N, ms=ms)
+    return time.perf_counter() - t0, frac
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def cpu_baseline(w, mstep=4):
+    sec, frac = oracle_sample(w, mstep)
+    return {"value": frac / sec, "unit": UNIT, "cores": host_cores(),
+            "kind": "oracle",
+            "sample": ("1 field-level pair of %s, zonal wavenumbers m = 0 mod %d "
+                       "(%.1f%% of the Legendre work), %.1f s, binary128 P table "
+                       "build included; plain CPU oracle (direct DFT + direct "
+                       "Legendre sums), not an optimised CPU SHT"
+                       % (w.name, mstep, 100 * frac, sec))}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1711_11296_gb300 import workloads as W
+    w = W.WORKLOADS[args.workload]
+    mstep = 16
+    for _ in range(args.warmup):
+        oracle_sample(w, mstep)
+    tot, frac = 0.0, 0.0
+    for _ in range(args.steps):
+        s, frac = oracle_sample(w, mstep)
+        tot += s
+    value = frac * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
+                   "field_levels": 1, "sample": "m = 0 mod %d" % mstep},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(),
+                         "kind": "oracle",
+                         "sample": "each step: 1 field-level pair, zonal "
+                                   "wavenumbers m = 0 mod %d (%.1f%% of the "
+                                   "Legendre work)" % (mstep, 100 * frac)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def native_arm(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    device = torch.device("cuda", local)
+
+    from paper_1711_11296_gb300 import sht, workloads as W
+    w = W.WORKLOADS[args.workload]
+    prec = "fp64" if args.precision == "auto" else args.precision
+    F = w.F
+    plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device)
+    a = W.workload_spectrum(w, F=F, field0=rank * F)
+    spec_in = torch.from_numpy(a).to(device=device, dtype=plan.complex_dtype)
+    grid = plan.empty_grid()
+    spec_out = plan.empty_spec()
+
+    def step():
+        plan.inverse(spec_in, out=grid)
+        plan.forward(grid, out=spec_out)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    plan.profile(True)
+    sampler.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    plan.profile(False)
+    prof = plan.profile_read()
+    ms_local = ev0.elapsed_time(ev1)
+    barrier(dist, local)
+    ms = max_over_ranks(dist, ms_local, device)
+    value = world * F * args.steps / (ms / 1000.0)
+    launches = sum(n for _, n in prof.values())
+
+    # roofline of the dominant kernel
+    pk, pk_src = peaks()
+    real_bytes = 8 if prec == "fp64" else 4
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, n) = dom
+    per_launch_s = tot_ms / n / 1000.0
+    if name.startswith("legendre") and prec == "fp64":
+        fl = legendre_flops(w, F)
+        roof = {"kernel": name + "_fp64", "bound": "alu",
+                "achieved": fl / per_launch_s / 1e12, "peak": 1.25,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured "
+                               "FP64 peak in MEASURED_PEAKS.json)"}
+    elif name.startswith("legendre"):
+        fl = legendre_flops(w, F) * {"bf16x2": 3, "fp16x2": 3, "bf16x3": 6,
+                                     "fp16x3": 6}[prec]
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"kernel": name + "_" + prec, "bound": "tensor",
+                "achieved": fl / per_launch_s / 1e12, "peak": peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "%s bf16 sustained" % pk_src}
+    else:
+        b = fft_bytes(w, F, real_bytes)
+        roof = {"kernel": name + ("_f64" if prec == "fp64" else "_f32"),
+                "bound": "hbm", "achieved": b / per_launch_s / 1e9,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "traffic": None,
+                "peak_source": "%s hbm_gbs" % pk_src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["ms_per_launch"] = 1000 * per_launch_s
+    stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}
+              for k, v in prof.items()}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.from_numpy(a).to(plan.complex_dtype).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dev_in = torch.empty_like(spec_in)
+
+        def e2e_step():
+            dev_in.copy_(host_in, non_blocking=True)
+            plan.inverse(dev_in, out=grid)
+            plan.forward(grid, out=spec_out)
+            host_out.copy_(spec_out, non_blocking=True)
+
+        for _ in range(max(args.warmup, 1)):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(dist, local)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
+        nbytes = host_in.numel() * host_in.element_size()
+        e2e = {"value": world * F * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32+" + prec,
+            "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
+                       "field_levels_per_gpu": F, "path": prec,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (grid %.1f GB)"
+                             % (F * w.J * w.I * real_bytes / 1e9)},
+            "roofline": roof, "stages": stages, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks, "gpu_launches": launches,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return native_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * sht.h -- C ABI of the GB300 spherical-harmonic transform on the nestable
+ * Clenshaw-Curtis (Fejer second rule) latitude grid of Hotta & Ujiie (2018).
+ *
+ * Every entry point takes plain pointers and sizes.  Device pointers are
+ * CUDA global-memory addresses on the device the plan was created on;
+ * streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ * All transforms are asynchronous on the given stream; they return after
+ * launching.  Errors are returned as negative sht_status codes and the
+ * message of the most recent error on the calling thread is available from
+ * sht_last_error().  No entry point falls back to the host: without a
+ * usable CUDA device plan creation fails with SHT_ERR_CUDA.
+ *
+ * Data layouts (shared by every transform):
+ *   grid      row-major [nfields][J][I], longitude fastest; latitude j = 0
+ *             is the northernmost node theta_1 = pi/(J+1)  (Eq. cc-points);
+ *             longitude i is lambda_i = 2 pi i / I            (Sec. 2).
+ *   spectrum  [ncoef][nfields] interleaved complex (re, im), fields fastest;
+ *             coefficient (m, n), 0 <= m <= n <= N, is row
+ *             m (N+1) - m (m-1)/2 + (n - m)   (triangular truncation N,
+ *             Eq. iSHT).  Only m >= 0 is stored: the fields are real, so
+ *             X_n^{-m} = conj(X_n^m).  Im(X_n^0) is ignored on input and
+ *             written as exactly 0 on output.
+ *   precision SHT_FP64: grid double, spectrum complex double.
+ *             split plans (SHT_BF16X*, SHT_FP16X*): grid float, spectrum
+ *             complex float; the Legendre contractions run on the tensor
+ *             cores as 2- or 3-term BF16/FP16 splits with FP32 accumulation.
+ *
+ * Normalisation (Eq. pnm-ortho, Eq. dFT): int_{-1}^{1} P~_n^m P~_{n'}^m dmu
+ * = delta_{nn'}, no Condon-Shortley phase; the forward zonal DFT carries
+ * 1/I and the inverse none, so sht_inverse(sht_forward(x)) = x for fields
+ * band-limited to N when J >= 2N+1 and I > 2N (Eq. cc-condition,
+ * Eq. fourier-condition).
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s* sht_plan_t;
+
+typedef enum {
+    SHT_FP64 = 0,   /* FP64 FFT and FP64 Legendre contraction            */
+    SHT_BF16X2 = 1, /* FP32 FFT; Legendre as 2-term BF16 split products  */
+    SHT_BF16X3 = 2, /* FP32 FFT; Legendre as 3-term BF16 split products  */
+    SHT_FP16X2 = 3, /* FP32 FFT; Legendre as 2-term FP16 split products  */
+    SHT_FP16X3 = 4  /* FP32 FFT; Legendre as 3-term FP16 split products  */
+} sht_precision;
+
+typedef enum {
+    SHT_OK = 0,
+    SHT_WARN_INEXACT = 1,    /* plan created, but J < 2N+1: the meridional
+                                quadrature is not exact (Eq. cc-condition) */
+    SHT_ERR_ARG = -1,        /* invalid argument (see each entry point)      */
+    SHT_ERR_ALLOC = -2,      /* device or host allocation failed             */
+    SHT_ERR_CUDA = -3,       /* a CUDA call or kernel launch failed          */
+    SHT_ERR_NOT_NESTED = -4, /* grids do not nest (Sec. 3.2)                 */
+    SHT_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up      */
+    SHT_ERR_HANDLE = -6,     /* NULL, destroyed or foreign plan handle       */
+    SHT_ERR_UNSUPPORTED = -7 /* valid request this build does not implement  */
+} sht_status;
+
+/* Create a plan for truncation N on the J x I Clenshaw-Curtis grid with
+ * nfields fields per call, on the current CUDA device.
+ *   N >= 0; J odd and >= 1 (the parity fold of Appendix B needs the Equator
+ *   node); I even and I > 2N (Eq. fourier-condition); I/2 must factor into
+ *   2, 3 and 5 with I <= 8192; nfields >= 1; precision a sht_precision.
+ * Builds on the device, once: the nodes (Eq. cc-points), the weights
+ * (Eq. cc-wgt), the table of P~_n^m at the northern nodes by the three-term
+ * recurrence (Sec. 4.1; FP64 with an extended exponent instead of the
+ * paper's quadruple precision), the FFT twiddles, the split-precision
+ * tables and a workspace of (N+1) * 2 * (J+1)/2 * nfields complex values.
+ * The plan owns all of it.  Returns SHT_OK, SHT_WARN_INEXACT (plan valid),
+ * SHT_ERR_ARG, SHT_ERR_ALLOC or SHT_ERR_CUDA; *out is set only on success. */
+int sht_plan_create(int N, int J, int I, int nfields, int precision,
+                    sht_plan_t* out);
+
+/* Free a plan and its device memory (synchronises the plan's device).
+ * NULL is a no-op returning SHT_OK; a destroyed handle gives SHT_ERR_HANDLE
+ * as long as its memory has not been reused. */
+int sht_plan_destroy(sht_plan_t plan);
+
+/* Plan parameters; any output pointer may be NULL.  exact = (J >= 2N+1). */
+int sht_plan_query(sht_plan_t plan, int* N, int* J, int* I, int* nfields,
+                   int* precision, int* exact, size_t* ncoef);
+
+/* Analysis, Eq. (dSHT) with the discretised Eq. (dFT) and Eq. (cc-quad):
+ * real FFT of every latitude row (x 1/I, m <= N kept), equatorial fold
+ * into symmetric/antisymmetric parts (Appendix B), then per m and parity
+ * the contraction with P~_n^m(mu_j) w_j over the (J+1)/2 northern nodes.
+ * grid: device, [nfields][J][I]; spec: device, [ncoef][nfields] complex.
+ * Buffers must not overlap.  One plan serves one stream at a time (the
+ * workspace is shared by its calls). */
+int sht_forward(sht_plan_t plan, const void* grid, void* spec, void* stream);
+
+/* Synthesis, Eq. (iSHT) via Eq. (iLT): per m and parity the contraction
+ * with P~_n^m(mu_j), unfold to both hemispheres (Appendix B), then the
+ * Hermitian inverse real FFT of every row (no scaling, m > N zero).
+ * spec: device [ncoef][nfields] complex; grid: device [nfields][J][I]. */
+int sht_inverse(sht_plan_t plan, const void* spec, void* grid, void* stream);
+
+/* Adjoints (transposes) for the plain inner products: the sum over grid
+ * points of x*y and the sum over stored coefficients of Re(conj(a) b).
+ *   which = 0: adjoint of sht_forward (spectrum -> grid):
+ *     x_ij = (w_j/I) sum_{m>=0} sum_n P~_n^m(mu_j) Re(a_n^m e^{i m lambda_i})
+ *   which = 1: adjoint of sht_inverse (grid -> spectrum):
+ *     a_n^m = c_m sum_j P~_n^m(mu_j) sum_i x_ij e^{-i m lambda_i},
+ *     c_0 = 1, c_m = 2 for m >= 1, Im(a_n^0) = 0.
+ * The paper defines no adjoint; these follow from Eq. (dSHT)/(iSHT).
+ * in/out: device buffers with the layouts above. */
+int sht_adjoint(sht_plan_t plan, int which, const void* in, void* out,
+                void* stream);
+
+/* Restriction of a fine grid to the coarse plan's spectrum (Sec. 3.2 and
+ * Appendix C): the coarse analysis of the sub-grid made of every 2^k-th
+ * latitude starting from j = 2^k (1-based) and every 2^k-th longitude,
+ * read in place by strided loads (no copy).  fine_grid: device
+ * [nfields][J_f][I_f] with J_f = 2^k (J+1) - 1 and I_f = 2^k I of the
+ * coarse plan; 1 <= k <= 8.  Returns SHT_ERR_ARG for a bad k. */
+int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
+                        void* coarse_spec, void* stream);
+
+/* Copy plan tables to host memory (test and inspection aid).  Any pointer
+ * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
+ * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,
+ * columns the northern nodes j = 0..(J-1)/2.  Synchronous. */
+int sht_plan_copy_tables(sht_plan_t plan, double* w, double* mu, double* pnm);
+
+/* Per-kernel timing (instrumentation, no counterpart in the paper).  With
+ * on != 0 every kernel the plan launches is bracketed by a pair of CUDA
+ * events recorded on the launch stream; off stops recording. */
+int sht_profile_enable(sht_plan_t plan, int on);
+
+/* Synchronise the recorded events and return, per stage, the summed device
+ * time in milliseconds and the number of launches since the last read,
+ * then reset.  ms and launches are host arrays of SHT_PROFILE_STAGES
+ * entries: 0 forward FFT (+fold), 1 forward Legendre, 2 inverse Legendre,
+ * 3 inverse FFT (+unfold), 4 split-precision operand conversion. */
+#define SHT_PROFILE_STAGES 8
+int sht_profile_read(sht_plan_t plan, double* ms, long long* launches);
+
+/* Message of the last error on this thread ("" if none). */
+const char* sht_last_error(void);
+
+/* Library version string. */
+const char* sht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

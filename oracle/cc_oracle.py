@@ -263,6 +263,19 @@ def synthesis(spec, N, J, I):
     return _synthesis_general(spec, N, J, I, lambda m: pnm_cc(N, J, m, m))
 
 
+def synthesis_rows(spec, N, J, I, rows):
+    """Synthesis (Eq. iSHT) evaluated only at the 1-based latitudes ``rows``
+    (all longitudes): returns real [F][len(rows)][I]."""
+    spec = np.asarray(spec, dtype=np.complex128)
+    F = spec.shape[1]
+    rows = np.asarray(rows)
+    X = np.zeros((F, len(rows), N + 1), dtype=np.complex128)
+    for m in range(N + 1):
+        a = spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
+        X[:, :, m] = legendre_inverse_m(a, pnm_cc(N, J, m, m, j=rows))
+    return dft_inverse(X, I)
+
+
 def analysis_gauss(x, N):
     """Forward SHT on a Gaussian grid (Eq. gauss-quad), J = x.shape[1]."""
     F, J, I = x.shape
@@ -358,4 +371,4 @@ def orthonormality_errors(N, J, m, pnm=None, w=None):
     return eN, eO
 
 
-__all__ += ["orthonormality_errors", "cc_node_binary128"]
+__all__ += ["orthonormality_errors", "cc_node_binary128", "synthesis_rows"]

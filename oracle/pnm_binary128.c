@@ -64,17 +64,20 @@ static void q_sincos(q_t x, q_t* s, q_t* c) {
  * by all points.  Returns 0, or -1 if scratch memory is unavailable. */
 static int pnm_rows(int N, int m_lo, int m_hi, const q_t* ct, const q_t* st,
                     int nj, double* out) {
-    size_t ncoef = (size_t)(N + 1) * (size_t)(N + 2) / 2;
-    q_t* eps = (q_t*)__builtin_malloc(sizeof(q_t) * ncoef);      /* eps_n^m  */
-    q_t* ieps = (q_t*)__builtin_malloc(sizeof(q_t) * ncoef);     /* 1/eps_n^m */
+    /* coefficients for the requested orders only: rows of m_lo..m_hi */
+    size_t nrow = 0;
+    for (int m = m_lo; m <= m_hi; ++m) nrow += (size_t)(N - m + 1);
+    q_t* eps = (q_t*)__builtin_malloc(sizeof(q_t) * (nrow ? nrow : 1));   /* eps_n^m  */
+    q_t* ieps = (q_t*)__builtin_malloc(sizeof(q_t) * (nrow ? nrow : 1));  /* 1/eps_n^m */
     q_t* amm = (q_t*)__builtin_malloc(sizeof(q_t) * (size_t)(N + 1));
     if (!eps || !ieps || !amm) {
         __builtin_free(eps); __builtin_free(ieps); __builtin_free(amm);
         return -1;
     }
-    size_t off = 0;
-    for (int m = 0; m <= N; ++m) {
+    for (int m = 0; m <= m_hi; ++m)
         amm[m] = m > 0 ? q_sqrt((q_t)(2 * m + 1) / (q_t)(2 * m)) : 0;
+    size_t off = 0;
+    for (int m = m_lo; m <= m_hi; ++m) {
         for (int n = m; n <= N; ++n) {
             q_t nn = (q_t)n, mm = (q_t)m;
             q_t e = n > m ? q_sqrt((nn * nn - mm * mm) / (4 * nn * nn - 1)) : 0;
@@ -88,23 +91,21 @@ static int pnm_rows(int N, int m_lo, int m_hi, const q_t* ct, const q_t* st,
     for (int jj = 0; jj < nj; ++jj) {
         q_t mu = ct[jj], s = st[jj];
         q_t p_mm = p00;                          /* P~_0^0 */
-        size_t row = 0, moff = 0;
+        size_t row = 0;                          /* = offset into eps/ieps */
         for (int m = 0; m <= m_hi; ++m) {
             if (m > 0) p_mm = amm[m] * s * p_mm;
-            if (m >= m_lo) {
-                out[row * (size_t)nj + jj] = (double)p_mm;
-                q_t p2 = 0, p1 = p_mm;           /* P~_{n-2}^m, P~_{n-1}^m */
-                for (int n = m + 1; n <= N; ++n) {
-                    /* eps_{m}^m = 0 makes n = m+1 the two-term start:
-                     * P~_{m+1}^m = mu P~_m^m / eps_{m+1}^m = sqrt(2m+3) mu P~_m^m */
-                    q_t pn = (mu * p1 - eps[moff + (size_t)(n - 1 - m)] * p2) *
-                             ieps[moff + (size_t)(n - m)];
-                    out[(row + (size_t)(n - m)) * (size_t)nj + jj] = (double)pn;
-                    p2 = p1; p1 = pn;
-                }
-                row += (size_t)(N - m + 1);
+            if (m < m_lo) continue;
+            out[row * (size_t)nj + jj] = (double)p_mm;
+            q_t p2 = 0, p1 = p_mm;               /* P~_{n-2}^m, P~_{n-1}^m */
+            for (int n = m + 1; n <= N; ++n) {
+                /* eps_{m}^m = 0 makes n = m+1 the two-term start:
+                 * P~_{m+1}^m = mu P~_m^m / eps_{m+1}^m = sqrt(2m+3) mu P~_m^m */
+                q_t pn = (mu * p1 - eps[row + (size_t)(n - 1 - m)] * p2) *
+                         ieps[row + (size_t)(n - m)];
+                out[(row + (size_t)(n - m)) * (size_t)nj + jj] = (double)pn;
+                p2 = p1; p1 = pn;
             }
-            moff += (size_t)(N - m + 1);
+            row += (size_t)(N - m + 1);
         }
     }
     __builtin_free(eps); __builtin_free(ieps); __builtin_free(amm);

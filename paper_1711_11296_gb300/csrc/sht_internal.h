@@ -1,0 +1,142 @@
+// Internal declarations of the GB300 Clenshaw-Curtis SHT library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sht.h"
+
+namespace sht {
+
+constexpr uint64_t kPlanMagic = 0x53485450'4C414E31ull;   // "SHTPLAN1"
+constexpr int kMaxRadixPasses = 16;
+constexpr int kMaxI = 8192;
+
+// Thread-local error message set by the C entry points.
+void set_error(const char* fmt, ...);
+
+template <typename T> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+
+// Mixed-radix factorisation of the half-length complex FFT (L = I/2).
+struct FftShape {
+    int L = 0;
+    int npass = 0;
+    int radix[kMaxRadixPasses] = {0};
+    int span[kMaxRadixPasses] = {0};   // M_p = L / (r_1 ... r_p)
+};
+
+// Row-source description for the forward FFT (plain or nested/strided).
+struct RowSource {
+    long long field_stride = 0;   // elements between fields
+    long long row_stride = 0;     // elements between consecutive (coarse) rows
+    long long row_offset = 0;     // element offset of row 0
+    int elem_stride = 1;          // elements between consecutive longitudes
+};
+
+// Scaling applied by the forward (analysis-type) FFT kernel.
+struct FwdScale {
+    const double* rowscale;   // [Jh] per northern row (w_j/I or 1), may be null
+    double mscale0;           // factor for m = 0
+    double mscale1;           // factor for m >= 1
+};
+
+// Scaling applied by the inverse (synthesis-type) FFT kernel.
+struct InvScale {
+    const double* rowscale;   // [Jh] per northern row (w_j/I or 1), may be null
+    double mfactor1;          // factor for m >= 1 before the Hermitian sum
+};
+
+struct SplitTables;   // tensor-core operand tables (split plans)
+
+enum Stage { kStageFftFwd = 0, kStageLegFwd = 1, kStageLegInv = 2,
+             kStageFftInv = 3, kStageSplitConv = 4 };
+
+// Optional per-launch event timing.
+struct Profiler {
+    bool on = false;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get();
+};
+
+}  // namespace sht
+
+struct sht_plan_s {
+    uint64_t magic;
+    int N, J, I, F, prec, exact;
+    int Jh;          // (J+1)/2 northern nodes incl. the Equator
+    int M;           // N+1 zonal wavenumbers
+    int device;
+    size_t ncoef;
+    int ldp;         // leading dimension of the P~ table (>= Jh)
+    int G;           // fields per FFT CTA
+    int fft_threads;
+    size_t fft_smem;
+    sht::FftShape fft;
+
+    // device tables (FP64)
+    double* d_mu;          // [Jh] cos(theta_j)
+    double* d_sin;         // [Jh] sin(theta_j)
+    double* d_w;           // [Jh] Clenshaw-Curtis weights
+    double* d_w_over_I;    // [Jh] w_j / I
+    double* d_eps;         // [ncoef] recurrence eps_n^m (host-built)
+    double* d_amm;         // [M] sqrt((2m+1)/(2m))
+    double* d_pnm;         // [ncoef][ldp] P~_n^m(mu_j), northern nodes
+    int* d_rev;            // [L] digit-reversed position of frequency k
+    void* d_tw;            // [L] e^{-2 pi i e / L}   (double2 or float2)
+    void* d_twpost;        // [L] e^{-2 pi i q / I}   (double2 or float2)
+    void* d_work;          // [M][2][Jh][F] complex Fourier workspace
+    size_t work_bytes;
+
+    // Legendre tile lists: int4 {m, parity, row0, col0}
+    int4* d_tiles_fwd; int ntiles_fwd;
+    int4* d_tiles_inv; int ntiles_inv;
+
+    sht::SplitTables* split;   // null for FP64 plans
+    sht::Profiler* prof;       // per-launch timing, off by default
+};
+
+namespace sht {
+
+bool plan_is_live(const sht_plan_s* p);
+
+// Bracket a launch with profiling events when the plan's profiler is on.
+struct ProfScope {
+    const sht_plan_s* p;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(const sht_plan_s* plan, int st, cudaStream_t stream);
+    ~ProfScope();
+};
+
+// tables
+cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s);
+cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s);
+cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
+
+// FFT launches
+cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,
+                               const RowSource& src, const FwdScale& sc,
+                               void* work, cudaStream_t s);
+cudaError_t launch_fft_inverse(const sht_plan_s* p, const void* work,
+                               const InvScale& sc, void* grid, cudaStream_t s);
+size_t fft_smem_bytes(int I, int G, bool fp64);
+
+// FP64 Legendre launches
+cudaError_t launch_legendre_fwd_fp64(const sht_plan_s* p, const double* work,
+                                     double* spec, cudaStream_t s);
+cudaError_t launch_legendre_inv_fp64(const sht_plan_s* p, const double* spec,
+                                     double* work, cudaStream_t s);
+
+__host__ __device__ inline size_t coef_offset(int N, int m) {
+    return (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
+}
+
+}  // namespace sht

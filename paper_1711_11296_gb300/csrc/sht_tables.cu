@@ -1,0 +1,177 @@
+// Plan-time tables: Clenshaw-Curtis nodes and weights, FFT twiddles and the
+// normalised associated Legendre functions at the northern nodes.
+#include <math.h>
+
+#include <vector>
+
+#include "sht_internal.h"
+
+namespace sht {
+
+// Nodes (Eq. cc-points) and weights (Eq. cc-wgt) of the northern half,
+// j = 1..(J+1)/2 (1-based), the Equator last.  theta_j = j pi/(J+1);
+// w_j = 4 sin(theta_j)/(J+1) sum_{p odd <= J} sin(p theta_j)/p, each
+// sin(p theta_j) taken after the exact integer reduction of p*j modulo
+// 2(J+1).  One thread per node; O(J) work each.
+__global__ void nodes_weights_kernel(int J, int Jh, int I, double* mu,
+                                     double* sn, double* w, double* w_over_I) {
+    const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j0 >= Jh) return;
+    const int j = j0 + 1;
+    double s, c;
+    if (2 * j == J + 1) {
+        s = 1.0;
+        c = 0.0;
+    } else {
+        sincospi((double)j / (double)(J + 1), &s, &c);
+    }
+    const long long period = 2LL * (J + 1);
+    double acc = 0.0;
+    for (int p = 1; p <= J; p += 2) {
+        const long long r = ((long long)p * j) % period;
+        acc += sinpi((double)r / (double)(J + 1)) / (double)p;
+    }
+    const double wj = 4.0 * s / (double)(J + 1) * acc;
+    mu[j0] = c;
+    sn[j0] = s;
+    w[j0] = wj;
+    w_over_I[j0] = wj / (double)I;
+}
+
+// out[e] = exp(-2 pi i e / denom), e < n, rounded to the element type.
+template <typename V>
+__global__ void twiddle_kernel(V* out, int n, int denom) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)denom, &s, &c);
+    V v;
+    v.x = c;
+    v.y = -s;
+    out[e] = v;
+}
+
+// P~_n^m(mu_j) for one (m, j) per thread, all n = m..N, by the standard
+// normalised three-term recurrence that Sec. 4.1 uses:
+//   P~_0^0 = 1/sqrt2, P~_m^m = a_m sin(theta) P~_{m-1}^{m-1},
+//   P~_n^m = (mu P~_{n-1}^m - eps_{n-1}^m P~_{n-2}^m) / eps_n^m.
+// The paper runs it in quadruple precision; here it runs in FP64 with an
+// extended exponent: the pair (value, e) stands for value * 2^(256 e), so
+// sin^m(theta) near the poles (down to ~1e-1670 at T639) does not underflow
+// before the n-recurrence has grown it back into range.  Entries whose true
+// value is below the FP64 range come out as subnormals or zero.
+__global__ void pnm_kernel(int N, int Jh, int ldp, const double* __restrict__ mu,
+                           const double* __restrict__ sn,
+                           const double* __restrict__ amm,
+                           const double* __restrict__ eps,
+                           double* __restrict__ pnm) {
+    const int jh = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    if (jh >= Jh) return;
+    const double BIG = 0x1p256, IBIG = 0x1p-256;
+    const double x = mu[jh], s = sn[jh];
+    double p = 0.70710678118654752440;   // P~_0^0
+    int e = 0;
+    for (int k = 1; k <= m; ++k) {
+        p *= amm[k] * s;
+        if (fabs(p) < IBIG) {
+            p *= BIG;
+            --e;
+        }
+    }
+    const size_t row0 = coef_offset(N, m);
+    auto value = [&](double v, int ex) -> double {
+        if (ex == 0) return v;
+        if (ex < -5) return 0.0;
+        for (int k = 0; k < -ex; ++k) v *= IBIG;
+        return v;
+    };
+    pnm[row0 * (size_t)ldp + jh] = value(p, e);
+    double p2 = 0.0, p1 = p;
+    // eps[] holds, per (m, n), eps_n^m at [row0 + n - m]; slot n = m (eps_m^m = 0)
+    // makes n = m+1 the two-term start.  ieps = 1/eps is stored after eps.
+    const double* ieps = eps + (size_t)(N + 1) * (N + 2) / 2;
+    for (int n = m + 1; n <= N; ++n) {
+        double pn = (x * p1 - eps[row0 + (n - 1 - m)] * p2) * ieps[row0 + (n - m)];
+        if (e < 0 && fabs(pn) >= BIG) {
+            pn *= IBIG;
+            p1 *= IBIG;
+            ++e;
+        }
+        pnm[(row0 + (size_t)(n - m)) * (size_t)ldp + jh] = value(pn, e);
+        p2 = p1;
+        p1 = pn;
+    }
+}
+
+cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s) {
+    const int threads = 128;
+    nodes_weights_kernel<<<(p->Jh + threads - 1) / threads, threads, 0, s>>>(
+        p->J, p->Jh, p->I, p->d_mu, p->d_sin, p->d_w, p->d_w_over_I);
+    return cudaGetLastError();
+}
+
+cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s) {
+    // Recurrence coefficients on the host (correctly rounded sqrt):
+    // eps_n^m = sqrt((n^2 - m^2)/(4 n^2 - 1)), 1/eps, a_m = sqrt((2m+1)/(2m)).
+    const int N = p->N;
+    const size_t nc = p->ncoef;
+    std::vector<double> eps(2 * nc, 0.0), amm(N + 1, 0.0);
+    for (int m = 0; m <= N; ++m) {
+        amm[m] = m > 0 ? sqrt((2.0 * m + 1.0) / (2.0 * m)) : 0.0;
+        const size_t r0 = coef_offset(N, m);
+        for (int n = m + 1; n <= N; ++n) {
+            const double nn = n, mm = m;
+            const double e = sqrt((nn * nn - mm * mm) / (4.0 * nn * nn - 1.0));
+            eps[r0 + (n - m)] = e;
+            eps[nc + r0 + (n - m)] = 1.0 / e;
+        }
+    }
+    cudaError_t err = cudaMemcpyAsync(p->d_eps, eps.data(), 2 * nc * sizeof(double),
+                                      cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemcpyAsync(p->d_amm, amm.data(), (N + 1) * sizeof(double),
+                          cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(p->d_pnm, 0, nc * (size_t)p->ldp * sizeof(double), s);
+    if (err != cudaSuccess) return err;
+    const int threads = 128;
+    dim3 grid((p->Jh + threads - 1) / threads, N + 1);
+    pnm_kernel<<<grid, threads, 0, s>>>(N, p->Jh, p->ldp, p->d_mu, p->d_sin,
+                                        p->d_amm, p->d_eps, p->d_pnm);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    // the host vectors must outlive the copies
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s) {
+    const int L = p->fft.L;
+    const int threads = 128;
+    const int blocks = (L + threads - 1) / threads;
+    if (p->prec == SHT_FP64) {
+        twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)p->d_tw, L, L);
+        twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)p->d_twpost, L, p->I);
+    } else {
+        twiddle_kernel<float2><<<blocks, threads, 0, s>>>((float2*)p->d_tw, L, L);
+        twiddle_kernel<float2><<<blocks, threads, 0, s>>>((float2*)p->d_twpost, L, p->I);
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    // digit-reversed output positions of the in-place mixed-radix FFT
+    std::vector<int> rev(L);
+    for (int k = 0; k < L; ++k) {
+        int kk = k, pos = 0;
+        for (int q = 0; q < p->fft.npass; ++q) {
+            pos += (kk % p->fft.radix[q]) * p->fft.span[q];
+            kk /= p->fft.radix[q];
+        }
+        rev[k] = pos;
+    }
+    err = cudaMemcpyAsync(p->d_rev, rev.data(), L * sizeof(int),
+                          cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return err;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace sht

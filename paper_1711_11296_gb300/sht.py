@@ -1,0 +1,182 @@
+"""PyTorch-facing wrapper of the C ABI: a ``Plan`` holding a native plan,
+and autograd Functions whose backward calls the native adjoints.
+
+PyTorch supplies device memory and the current CUDA stream; every step of
+every transform runs in the library's kernels.
+"""
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import PRECISION, SHTError, check, lib
+
+
+def _stream_ptr(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Plan:
+    """Spherical-harmonic transform plan on the J x I Clenshaw-Curtis grid.
+
+    Layouts: grid ``[nfields, J, I]`` real; spectrum ``[ncoef, nfields]``
+    complex (packed m-major, m >= 0 only).  ``precision`` is one of "fp64",
+    "bf16x2", "bf16x3", "fp16x2", "fp16x3"; FP64 plans use float64/complex128
+    tensors, split plans float32/complex64."""
+
+    def __init__(self, N, J, I, nfields, precision="fp64", device=None):
+        if precision not in PRECISION:
+            raise ValueError("precision must be one of %s" % list(PRECISION))
+        self.device = torch.device("cuda", torch.cuda.current_device()
+                                   if device is None else torch.device(device).index or 0)
+        self.N, self.J, self.I, self.F = N, J, I, nfields
+        self.precision = precision
+        self.real_dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.complex_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.ncoef = (N + 1) * (N + 2) // 2
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = check(lib.sht_plan_create(N, J, I, nfields, PRECISION[precision],
+                                           ctypes.byref(h)))
+        self.exact = rc == _native.SHT_OK
+        self._h = h
+
+    # -- buffers ----------------------------------------------------------
+    def _check(self, t, shape, dtype, name):
+        if not isinstance(t, torch.Tensor) or t.device != self.device:
+            raise ValueError("%s must be a tensor on %s" % (name, self.device))
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+            raise ValueError("%s must be %s %s, got %s %s" % (
+                name, dtype, tuple(shape), t.dtype, tuple(t.shape)))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+
+    def empty_grid(self):
+        return torch.empty((self.F, self.J, self.I), dtype=self.real_dtype,
+                           device=self.device)
+
+    def empty_spec(self):
+        return torch.empty((self.ncoef, self.F), dtype=self.complex_dtype,
+                           device=self.device)
+
+    # -- transforms -----------------------------------------------------------
+    def forward(self, grid, out=None):
+        """Analysis: grid [F, J, I] -> spectrum [ncoef, F]."""
+        self._check(grid, (self.F, self.J, self.I), self.real_dtype, "grid")
+        out = self.empty_spec() if out is None else out
+        self._check(out, (self.ncoef, self.F), self.complex_dtype, "spec")
+        check(lib.sht_forward(self._h, ctypes.c_void_p(grid.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()),
+                              _stream_ptr(self.device)))
+        return out
+
+    def inverse(self, spec, out=None):
+        """Synthesis: spectrum [ncoef, F] -> grid [F, J, I]."""
+        self._check(spec, (self.ncoef, self.F), self.complex_dtype, "spec")
+        out = self.empty_grid() if out is None else out
+        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        check(lib.sht_inverse(self._h, ctypes.c_void_p(spec.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()),
+                              _stream_ptr(self.device)))
+        return out
+
+    def adjoint(self, which, x, out=None):
+        """which=0: adjoint of forward (spectrum -> grid);
+        which=1: adjoint of inverse (grid -> spectrum)."""
+        if which == 0:
+            self._check(x, (self.ncoef, self.F), self.complex_dtype, "spec")
+            out = self.empty_grid() if out is None else out
+            self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        elif which == 1:
+            self._check(x, (self.F, self.J, self.I), self.real_dtype, "grid")
+            out = self.empty_spec() if out is None else out
+            self._check(out, (self.ncoef, self.F), self.complex_dtype, "spec")
+        else:
+            raise ValueError("which must be 0 or 1")
+        check(lib.sht_adjoint(self._h, which, ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()),
+                              _stream_ptr(self.device)))
+        return out
+
+    def restrict_nested(self, fine_grid, k, out=None):
+        """Coarse spectrum of a fine grid with J_f = 2^k (J+1) - 1, I_f = 2^k I."""
+        Jf, If = 2 ** k * (self.J + 1) - 1, 2 ** k * self.I
+        self._check(fine_grid, (self.F, Jf, If), self.real_dtype, "fine_grid")
+        out = self.empty_spec() if out is None else out
+        self._check(out, (self.ncoef, self.F), self.complex_dtype, "spec")
+        check(lib.sht_restrict_nested(self._h, ctypes.c_void_p(fine_grid.data_ptr()),
+                                      k, ctypes.c_void_p(out.data_ptr()),
+                                      _stream_ptr(self.device)))
+        return out
+
+    def tables(self):
+        """(w [J], mu [J], pnm [ncoef, (J+1)/2]) copied from the device."""
+        import numpy as np
+        Jh = (self.J + 1) // 2
+        w = np.empty(self.J)
+        mu = np.empty(self.J)
+        pnm = np.empty((self.ncoef, Jh))
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(lib.sht_plan_copy_tables(self._h, w.ctypes.data_as(dp),
+                                       mu.ctypes.data_as(dp), pnm.ctypes.data_as(dp)))
+        return w, mu, pnm
+
+    def profile(self, on=True):
+        """Turn per-launch event timing on or off."""
+        check(lib.sht_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{stage: (total_ms, launches)} since the last read (synchronises)."""
+        ms = (ctypes.c_double * _native.PROFILE_STAGES)()
+        n = (ctypes.c_longlong * _native.PROFILE_STAGES)()
+        check(lib.sht_profile_read(self._h, ms, n))
+        return {_native.STAGE_NAMES[k]: (ms[k], n[k])
+                for k in range(_native.PROFILE_STAGES) if n[k]}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.sht_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Analysis(torch.autograd.Function):
+    """grid -> spectrum with the native adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, grid, plan):
+        ctx.plan = plan
+        return plan.forward(grid.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.adjoint(0, g.contiguous()), None
+
+
+class Synthesis(torch.autograd.Function):
+    """spectrum -> grid with the native adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, spec, plan):
+        ctx.plan = plan
+        return plan.inverse(spec.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.adjoint(1, g.contiguous()), None
+
+
+def analysis(grid, plan):
+    return Analysis.apply(grid, plan)
+
+
+def synthesis(spec, plan):
+    return Synthesis.apply(spec, plan)
+
+
+__all__ = ["Plan", "Analysis", "Synthesis", "analysis", "synthesis", "SHTError"]

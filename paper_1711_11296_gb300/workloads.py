@@ -121,3 +121,10 @@ def random_grid(F, J, I, seed=SEED_BASE + 7):
     tests, where any input is valid)."""
     g = np.random.Generator(np.random.PCG64(seed))
     return g.standard_normal((F, J, I))
+
+
+def random_grid_field(f, J, I, seed=SEED_BASE + 17):
+    """Field f of a seeded grid, reproducible one field at a time: [J][I]
+    standard normal values from seed + f."""
+    g = np.random.Generator(np.random.PCG64(seed + f))
+    return g.standard_normal((J, I))

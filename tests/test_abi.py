@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every entry point include/sht.h declares, and
+rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from sht_testutil import built_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(sht_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = built_lib()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "sht_forward" in names and "sht_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_lists_match_header(lib):
+    from paper_1711_11296_gb300 import _native
+    assert sorted(_native.EXPORTED) == _declared()
+
+
+@pytest.mark.parametrize("args,code", [
+    ((-1, 3, 4, 1, 0), -1),        # N < 0
+    ((3, 8, 16, 1, 0), -1),        # J even
+    ((10, 21, 20, 1, 0), -1),      # I <= 2N
+    ((10, 21, 21, 1, 0), -1),      # I odd
+    ((10, 21, 28, 1, 0), -1),      # I/2 = 14 has the factor 7
+    ((10, 21, 24, 0, 0), -1),      # nfields < 1
+    ((10, 21, 24, 1, 9), -1),      # unknown precision
+    ((10, 21, 16384, 1, 0), -1),   # I too large
+])
+def test_invalid_plan_arguments_rejected_on_host(lib, args, code):
+    h = ctypes.c_void_p()
+    lib.sht_plan_create.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.sht_plan_create(*args, ctypes.byref(h)) == code
+    lib.sht_last_error.restype = ctypes.c_char_p
+    assert lib.sht_last_error()
+
+
+def test_null_and_foreign_handles(lib):
+    vp = ctypes.c_void_p
+    lib.sht_forward.argtypes = [vp, vp, vp, vp]
+    lib.sht_plan_destroy.argtypes = [vp]
+    assert lib.sht_plan_destroy(None) == 0
+    assert lib.sht_forward(None, None, None, None) == -6
+    bogus = ctypes.create_string_buffer(256)
+    assert lib.sht_forward(ctypes.addressof(bogus), None, None, None) == -6
+    assert lib.sht_plan_destroy(ctypes.addressof(bogus)) == -6
