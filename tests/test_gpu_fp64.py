@@ -43,9 +43,13 @@ def test_tables_match_oracle(sht, N, J, I, F):
     np.testing.assert_allclose(mu, O.cc_nodes(J)[1], rtol=0, atol=4e-16)
     Jh = (J + 1) // 2
     ref = O.pnm_cc(N, J, j=np.arange(1, Jh + 1))
-    big = np.abs(ref) > 1e-250
-    np.testing.assert_allclose(pnm[big], ref[big], rtol=2e-13, atol=0)
-    assert np.abs(pnm[~big]).max(initial=0) < 1e-249
+    # The device evaluates P~ at the FP64-rounded node (|d mu| <= 1.1e-16)
+    # while the oracle uses the binary128 node; with |dP~/dmu| up to ~n^2
+    # times the row scale, entries can differ by ~1e-13 of the row maximum
+    # (relative differences blow up only near zeros of P~).
+    rowmax = np.abs(ref).max(axis=1, keepdims=True)
+    assert (np.abs(pnm - ref) <= 1e-12 * rowmax).all(), \
+        np.max(np.abs(pnm - ref) / rowmax)
 
 
 @pytest.mark.parametrize("N,J,I,F", CASES)
