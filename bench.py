@@ -41,6 +41,8 @@ def parse_args():
     ap.add_argument("--workload", default="T639")
     ap.add_argument("--precision", default="auto",
                     help="auto (headline path), fp64, bf16x3, ...")
+    ap.add_argument("--fields", type=int, default=0,
+                    help="field-levels per GPU (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -254,7 +256,7 @@ def native_arm(args):
     from paper_1711_11296_gb300 import sht, workloads as W
     w = W.WORKLOADS[args.workload]
     prec = "fp64" if args.precision == "auto" else args.precision
-    F = w.F
+    F = args.fields if args.fields > 0 else w.F
     plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device)
     a = W.workload_spectrum(w, F=F, field0=rank * F)
     spec_in = torch.from_numpy(a).to(device=device, dtype=plan.complex_dtype)

@@ -40,7 +40,9 @@ def test_tables_match_oracle(sht, N, J, I, F):
     assert p.exact == (J >= 2 * N + 1)
     w, mu, pnm = p.tables()
     np.testing.assert_allclose(w, O.cc_weights(J), rtol=0, atol=2e-15)
-    np.testing.assert_allclose(mu, O.cc_nodes(J)[1], rtol=0, atol=4e-16)
+    # the device mirrors the southern nodes exactly (mu_{J+1-j} = -mu_j);
+    # the oracle rounds each cos separately: allow 1e-15
+    np.testing.assert_allclose(mu, O.cc_nodes(J)[1], rtol=0, atol=1e-15)
     Jh = (J + 1) // 2
     ref = O.pnm_cc(N, J, j=np.arange(1, Jh + 1))
     # The device evaluates P~ at the FP64-rounded node (|d mu| <= 1.1e-16)
