@@ -124,6 +124,30 @@ int sht_adjoint(sht_plan_t plan, int which, const void* in, void* out,
 int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
                         void* coarse_spec, void* stream);
 
+/* Allocation-free FP64 analysis, for callers that cannot allocate device
+ * memory (no counterpart in the paper, which has no notion of memory
+ * management): for example a plug-in inside an application that owns all
+ * of the GPU's memory through its own pool, or code that runs where the
+ * application forbids allocations.  Such a caller cannot create a plan, so
+ * this call needs none: it computes the same result as sht_forward on an
+ * FP64 plan of these sizes, rebuilding the nodes, weights, P~ table, FFT
+ * tables and Fourier workspace in one fixed scratch array of
+ * SHT_NOALLOC_SCRATCH_BYTES that the library keeps on every device that
+ * loads it, for the life of the process.  It calls no allocator.
+ *   grid: device double [nfields][J][I]; spec: device complex double
+ *   [ncoef][nfields]; size rules as for sht_plan_create.  Sizes whose
+ *   tables and workspace exceed the scratch array are rejected with
+ *   SHT_ERR_ARG and a message giving the bytes needed (T127 with J = 257,
+ *   I = 512 fits up to 46 fields).
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call overwrites the array: calls that overlap on the GPU race, so
+ * serialise them (one stream, or events).  Each call rewrites every entry
+ * it reads, so results never depend on an earlier call. */
+#define SHT_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int sht_forward_noalloc(int N, int J, int I, int nfields, const double* grid,
+                        double* spec, void* stream);
+
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
  * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,

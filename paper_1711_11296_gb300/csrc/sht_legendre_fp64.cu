@@ -176,3 +176,50 @@ cudaError_t launch_legendre_inv_fp64(const sht_plan_s* p, const double* spec,
 }
 
 }  // namespace sht
+
+namespace sht {
+namespace {
+
+// One thread per zonal wavenumber m: its tiles start after those of all
+// m' < m (same order and geometry as build_legendre_tiles).
+__global__ void fwd_tiles_kernel(int N, int C, int4* tiles) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > N) return;
+    const int nct = (C + BN - 1) / BN;
+    auto rows = [&](int mm, int q) {
+        const int d = N - mm - q;
+        return d >= 0 ? d / 2 + 1 : 0;
+    };
+    long long off = 0;
+    for (int mm = 0; mm < m; ++mm)
+        off += (long long)((rows(mm, 0) + BM - 1) / BM + (rows(mm, 1) + BM - 1) / BM) * nct;
+    for (int q = 0; q < 2; ++q) {
+        const int R = rows(m, q);
+        for (int r0 = 0; r0 < R; r0 += BM)
+            for (int c0 = 0; c0 < C; c0 += BN) tiles[off++] = make_int4(m, q, r0, c0);
+    }
+}
+
+}  // namespace
+
+// Number of forward Legendre tiles for truncation N and C real columns.
+int legendre_fwd_tile_count(int N, int C) {
+    long long n = 0;
+    const int nct = (C + BN - 1) / BN;
+    for (int m = 0; m <= N; ++m)
+        for (int q = 0; q < 2; ++q) {
+            const int d = N - m - q;
+            const int R = d >= 0 ? d / 2 + 1 : 0;
+            n += (long long)((R + BM - 1) / BM) * nct;
+        }
+    return (int)n;
+}
+
+// Build the forward tile list on the device (no host memory involved).
+cudaError_t launch_build_fwd_tiles(int N, int C, int4* tiles, cudaStream_t s) {
+    const int threads = 128;
+    fwd_tiles_kernel<<<(N + 1 + threads - 1) / threads, threads, 0, s>>>(N, C, tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace sht

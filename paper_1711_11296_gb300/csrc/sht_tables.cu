@@ -175,3 +175,27 @@ cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s) {
 }
 
 }  // namespace sht
+
+namespace sht {
+
+// Launch only the P~ recurrence kernel; the caller has filled p->d_eps
+// (eps and 1/eps, 2*ncoef doubles), p->d_amm, p->d_mu and p->d_sin.
+cudaError_t launch_pnm_recurrence(const sht_plan_s* p, cudaStream_t s) {
+    const int threads = 128;
+    dim3 grid((p->Jh + threads - 1) / threads, p->N + 1);
+    pnm_kernel<<<grid, threads, 0, s>>>(p->N, p->Jh, p->ldp, p->d_mu, p->d_sin,
+                                        p->d_amm, p->d_eps, p->d_pnm);
+    return cudaGetLastError();
+}
+
+// Launch only the two twiddle-table kernels (FP64 plans).
+cudaError_t launch_twiddles_fp64(const sht_plan_s* p, cudaStream_t s) {
+    const int L = p->fft.L;
+    const int threads = 128;
+    const int blocks = (L + threads - 1) / threads;
+    twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)p->d_tw, L, L);
+    twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)p->d_twpost, L, p->I);
+    return cudaGetLastError();
+}
+
+}  // namespace sht
