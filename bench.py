@@ -45,6 +45,8 @@ def parse_args():
                     help="field-levels per GPU (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 comparison path")
     return ap.parse_args()
 
 
@@ -246,17 +248,79 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
-def native_arm(args):
-    import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = dist_init(world, "nccl")
-    device = torch.device("cuda", local)
+def split_gemm_bytes(w, F, prec, inverse):
+    """Algorithmic HBM bytes of one split Legendre launch: the FP32 operand
+    read once, the BF16 term planes of the P table read once (rows padded to
+    8, K to 32), the FP32 result written once."""
+    terms = 2 if prec.endswith("x2") else 3
+    Jh = (w.J + 1) // 2
+    C = 2 * F
+    ncoef = (w.N + 1) * (w.N + 2) // 2
+    work = (w.N + 1) * 2 * Jh * C * 4
+    spec = ncoef * C * 4
+    tab = 0
+    for m in range(w.N + 1):
+        for q in range(2):
+            d = w.N - m - q
+            R = d // 2 + 1 if d >= 0 else 0
+            if inverse:
+                tab += ((Jh + 7) // 8 * 8) * ((R + 31) // 32 * 32) * 2
+            elif R:
+                tab += ((R + 7) // 8 * 8) * ((Jh + 31) // 32 * 32) * 2
+    tab *= terms
+    return (spec + tab + work)
 
+
+def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
+    per_launch_s = tot_ms / n / 1000.0
+    real_bytes = 8 if prec == "fp64" else 4
+    if name.startswith("legendre") and prec == "fp64":
+        fl = legendre_flops(w, F)
+        roof = {"kernel": name + "_fp64", "bound": "alu",
+                "achieved": fl / per_launch_s / 1e12, "peak": 1.25,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured "
+                               "FP64 peak in MEASURED_PEAKS.json)"}
+    elif name.startswith("legendre"):
+        products = 3 if prec.endswith("x2") else 6
+        fl = legendre_flops(w, F) * products
+        by = split_gemm_bytes(w, F, prec, name.endswith("inverse"))
+        t_frac = fl / per_launch_s / 1e12 / pk["bf16_tflops_sustained"]
+        h_frac = by / per_launch_s / 1e9 / pk["hbm_gbs"]
+        if h_frac >= t_frac:
+            roof = {"kernel": name + "_" + prec, "bound": "hbm",
+                    "achieved": by / per_launch_s / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "traffic": None,
+                    "peak_source": "%s hbm_gbs" % pk_src,
+                    "tensor_frac": t_frac}
+        else:
+            roof = {"kernel": name + "_" + prec, "bound": "tensor",
+                    "achieved": fl / per_launch_s / 1e12,
+                    "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                    "traffic": None,
+                    "peak_source": "%s bf16_tflops_sustained" % pk_src,
+                    "hbm_frac": h_frac}
+    else:
+        b = fft_bytes(w, F, real_bytes)
+        if prec == "fp64":
+            roof = {"kernel": name + "_f64", "bound": "alu",
+                    "achieved": b / per_launch_s / 1e9, "peak": None,
+                    "unit": "GB/s", "traffic": None,
+                    "peak_source": "FP64 pipe bound; HBM figure for context"}
+        else:
+            roof = {"kernel": name + "_f32", "bound": "hbm",
+                    "achieved": b / per_launch_s / 1e9, "peak": pk["hbm_gbs"],
+                    "unit": "GB/s", "traffic": None,
+                    "peak_source": "%s hbm_gbs" % pk_src}
+    if roof["peak"]:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["ms_per_launch"] = 1000 * per_launch_s
+    return roof
+
+
+def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
+    import torch
     from paper_1711_11296_gb300 import sht, workloads as W
-    w = W.WORKLOADS[args.workload]
-    prec = "fp64" if args.precision == "auto" else args.precision
-    F = args.fields if args.fields > 0 else w.F
     plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device)
     a = W.workload_spectrum(w, F=F, field0=rank * F)
     spec_in = torch.from_numpy(a).to(device=device, dtype=plan.complex_dtype)
@@ -272,7 +336,6 @@ def native_arm(args):
     torch.cuda.synchronize()
     barrier(dist, local)
     torch.cuda.synchronize()
-
     stream = torch.cuda.current_stream(device)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -287,47 +350,14 @@ def native_arm(args):
     clocks = sampler.stop()
     plan.profile(False)
     prof = plan.profile_read()
+    plan.status()
     ms_local = ev0.elapsed_time(ev1)
     barrier(dist, local)
     ms = max_over_ranks(dist, ms_local, device)
-    value = world * F * args.steps / (ms / 1000.0)
-    launches = sum(n for _, n in prof.values())
+    res = {"ms": ms, "prof": prof, "clocks": clocks,
+           "launches": sum(n for _, n in prof.values())}
 
-    # roofline of the dominant kernel
-    pk, pk_src = peaks()
-    real_bytes = 8 if prec == "fp64" else 4
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    name, (tot_ms, n) = dom
-    per_launch_s = tot_ms / n / 1000.0
-    if name.startswith("legendre") and prec == "fp64":
-        fl = legendre_flops(w, F)
-        roof = {"kernel": name + "_fp64", "bound": "alu",
-                "achieved": fl / per_launch_s / 1e12, "peak": 1.25,
-                "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured "
-                               "FP64 peak in MEASURED_PEAKS.json)"}
-    elif name.startswith("legendre"):
-        fl = legendre_flops(w, F) * {"bf16x2": 3, "fp16x2": 3, "bf16x3": 6,
-                                     "fp16x3": 6}[prec]
-        peak = pk["bf16_tflops_sustained"]
-        roof = {"kernel": name + "_" + prec, "bound": "tensor",
-                "achieved": fl / per_launch_s / 1e12, "peak": peak,
-                "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "%s bf16 sustained" % pk_src}
-    else:
-        b = fft_bytes(w, F, real_bytes)
-        roof = {"kernel": name + ("_f64" if prec == "fp64" else "_f32"),
-                "bound": "hbm", "achieved": b / per_launch_s / 1e9,
-                "peak": pk["hbm_gbs"], "unit": "GB/s", "traffic": None,
-                "peak_source": "%s hbm_gbs" % pk_src}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["ms_per_launch"] = 1000 * per_launch_s
-    stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]}
-              for k, v in prof.items()}
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if not args.no_e2e:
+    if e2e_wanted:
         host_in = torch.from_numpy(a).to(plan.complex_dtype).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
         dev_in = torch.empty_like(spec_in)
@@ -349,8 +379,48 @@ def native_arm(args):
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
         nbytes = host_in.numel() * host_in.element_size()
-        e2e = {"value": world * F * args.steps / (e2e_ms / 1000.0), "unit": UNIT,
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        res["e2e"] = {"value": world * F * args.steps / (e2e_ms / 1000.0),
+                      "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                      "d2h_bytes_per_step": nbytes}
+    plan.close()
+    del spec_in, grid, spec_out
+    torch.cuda.empty_cache()
+    return res
+
+
+def native_arm(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    device = torch.device("cuda", local)
+
+    from paper_1711_11296_gb300 import workloads as W
+    w = W.WORKLOADS[args.workload]
+    prec = "bf16x3" if args.precision == "auto" else args.precision
+    F = args.fields if args.fields > 0 else w.F
+    pk, pk_src = peaks()
+
+    head = run_path(args, w, F, prec, device, dist, local, rank, world,
+                    not args.no_e2e)
+    value = world * F * args.steps / (head["ms"] / 1000.0)
+    prof = head["prof"]
+    name, (tot_ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
+    roof = roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src)
+    stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                  "roofline": roofline_for(k, v[0], v[1], w, F, prec, pk, pk_src)}
+              for k, v in prof.items()}
+
+    other = None
+    if prec != "fp64" and args.precision == "auto" and not args.no_fp64:
+        r64 = run_path(args, w, F, "fp64", device, dist, local, rank, world, False)
+        n64, (t64, c64) = max(r64["prof"].items(), key=lambda kv: kv[1][0])
+        other = {"path": "fp64",
+                 "value": world * F * args.steps / (r64["ms"] / 1000.0),
+                 "ms_per_step": r64["ms"] / args.steps,
+                 "roofline": roofline_for(n64, t64, c64, w, F, "fp64", pk, pk_src),
+                 "gpu_launches": r64["launches"]}
+        other["split_speedup"] = value / other["value"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -360,7 +430,7 @@ def native_arm(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "ms_per_step": head["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == "fp64" else "f32+" + prec,
             "data": "synthetic",
@@ -368,12 +438,12 @@ def native_arm(args):
                        "field_levels_per_gpu": F, "path": prec,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (grid %.1f GB)"
-                             % (F * w.J * w.I * real_bytes / 1e9)},
-            "roofline": roof, "stages": stages, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clocks, "gpu_launches": launches,
+                             % (F * w.J * w.I * (8 if prec == "fp64" else 4) / 1e9)},
+            "roofline": roof, "stages": stages, "fp64_path": other,
+            "cpu_baseline": cpu, "e2e": head.get("e2e"),
+            "clocks": head["clocks"], "gpu_launches": head["launches"],
         }
         print(json.dumps(line))
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

@@ -148,6 +148,12 @@ int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
 int sht_forward_noalloc(int N, int J, int I, int nfields, const double* grid,
                         double* spec, void* stream);
 
+/* Synchronise the plan's device and report device-side failures of the
+ * plan's kernels since the last call: SHT_ERR_TIMEOUT if a tensor-core
+ * kernel gave up on one of its bounded waits (its outputs are then
+ * invalid), SHT_OK otherwise.  Clears the recorded status. */
+int sht_plan_status(sht_plan_t plan);
+
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
  * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,

@@ -23,6 +23,7 @@ cudaError_t launch_legendre_fwd_split(const sht_plan_s* p, const void* work,
                                       void* spec, cudaStream_t s);
 cudaError_t launch_legendre_inv_split(const sht_plan_s* p, const void* spec,
                                       void* work, cudaStream_t s);
+int split_status_read_and_clear(const sht_plan_s* p);
 
 namespace {
 thread_local std::string g_error;
@@ -311,11 +312,12 @@ int forward_scaled(sht_plan_t p, const void* grid, const RowSource& src,
         e = launch_fft_forward(p, grid, src, sc, p->d_work, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward FFT launch");
-    if (p->prec == SHT_FP64) {
+    {
         ProfScope ps(p, kStageLegFwd, s);
-        e = launch_legendre_fwd_fp64(p, (const double*)p->d_work, (double*)spec, s);
-    } else {
-        e = launch_legendre_fwd_split(p, p->d_work, spec, s);
+        if (p->prec == SHT_FP64)
+            e = launch_legendre_fwd_fp64(p, (const double*)p->d_work, (double*)spec, s);
+        else
+            e = launch_legendre_fwd_split(p, p->d_work, spec, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "forward Legendre launch");
     return SHT_OK;
@@ -330,11 +332,12 @@ int forward_impl(sht_plan_t p, const void* grid, const RowSource& src, void* spe
 int inverse_impl(sht_plan_t p, const void* spec, const InvScale& sc, void* grid,
                  cudaStream_t s) {
     cudaError_t e;
-    if (p->prec == SHT_FP64) {
+    {
         ProfScope ps(p, kStageLegInv, s);
-        e = launch_legendre_inv_fp64(p, (const double*)spec, (double*)p->d_work, s);
-    } else {
-        e = launch_legendre_inv_split(p, spec, p->d_work, s);
+        if (p->prec == SHT_FP64)
+            e = launch_legendre_inv_fp64(p, (const double*)spec, (double*)p->d_work, s);
+        else
+            e = launch_legendre_inv_split(p, spec, p->d_work, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "inverse Legendre launch");
     {
@@ -478,4 +481,19 @@ extern "C" int sht_profile_read(sht_plan_t p, double* ms, long long* launches) {
     }
     p->prof->recs.clear();
     return status;
+}
+
+extern "C" int sht_plan_status(sht_plan_t p) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    DeviceGuard dg(p->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise");
+    const int v = split_status_read_and_clear(p);
+    if (v < 0) return cuda_fail(cudaGetLastError(), "status read");
+    if (v) {
+        set_error("a tensor-core kernel gave up waiting (bounded wait expired)");
+        return SHT_ERR_TIMEOUT;
+    }
+    return SHT_OK;
 }

@@ -1,20 +1,571 @@
-// Split-precision (BF16/FP16 tensor-core) Legendre path.
+// Split-precision Legendre contractions on the 5th-generation tensor cores
+// (tcgen05 + TMEM), for split plans (FP32 grid and spectrum).
+//
+// Both directions are per-(m, parity) products D = A . B over K, with the
+// same shape as the FP64 path (Eq. cc-quad and Eq. iLT in the parity form
+// of Appendix B):
+//   forward  D[r][c] = sum_{j}  P~_{n_r}^m(mu_j)  Bw[j][c]     A: rows n_r, K = j
+//   inverse  D[j][c] = sum_{r}  P~_{n_r}^m(mu_j)  X_{n_r}[c]    A: rows j,  K = r
+// where c runs over the 2F real columns.  Operands are split into T = 2 or
+// 3 BF16 terms, x = x_1 + x_2 (+ x_3), x_{t+1} = bf16(x - x_1 - .. - x_t),
+// and the products x_a y_b with a + b <= T - 1 (0-based) are accumulated in
+// one FP32 accumulator in tensor memory (3 products for T = 2, 6 for T = 3).
+//
+// A (the P~ table) is split once at plan time and stored pre-tiled in the
+// canonical no-swizzle K-major layout of the tensor-core shared-memory
+// descriptor: 8 x 8 core matrices of 128 contiguous bytes, core (i8, k8)
+// at ((i8 * TK/8) + k8) * 128 within a K-slab of TK = 32.  A 128-row tile
+// of a slab is therefore one contiguous block that one bulk asynchronous
+// copy (TMA engine, cp.async.bulk) moves into shared memory.
+// B (the FP32 Fourier data or spectrum) stays FP32 in HBM; four converter
+// warps load it coalesced, split it into BF16 terms and store it directly
+// in the same K-major core-matrix layout.
+//
+// One CTA computes a 128 x 256 output tile: warps 0-3 convert B and run the
+// epilogue (tcgen05.ld of their 32 TMEM lanes each), warp 4 issues the bulk
+// copies of A, one thread of warp 5 issues tcgen05.mma (M = 128, N = 256,
+// K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
+// a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
+// waits (bounded) for its MMAs and frees its tensor memory.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <vector>
+
 #include "sht_internal.h"
 
 namespace sht {
 
-struct SplitTables {};
+struct SplitProb {
+    long long a_off;   // byte offset of this problem's A block in each term plane
+    long long b_off;   // float offset of B row 0
+    long long o_off;   // float offset of output row 0
+    int R8;            // A rows padded to 8 (K-slab height)
+    int Mrows;         // valid output rows
+    int K;             // valid K (rows of B)
+    int nkt;           // K tiles of TK
+    int b_stride;      // floats between B rows
+    int o_stride;      // floats between output rows
+};
 
-cudaError_t split_tables_create(sht_plan_s*, cudaStream_t) {
-    set_error("split-precision plans are not available in this build");
-    return cudaErrorNotSupported;
+struct SplitTables {
+    int terms = 3;
+    unsigned char* fwd_planes = nullptr;   // terms planes of fwd_plane_bytes
+    size_t fwd_plane_bytes = 0;
+    unsigned char* inv_planes = nullptr;
+    size_t inv_plane_bytes = 0;
+    SplitProb* d_probs_fwd = nullptr;
+    SplitProb* d_probs_inv = nullptr;
+    int4* d_tiles_fwd = nullptr;
+    int4* d_tiles_inv = nullptr;
+    int ntiles_fwd = 0, ntiles_inv = 0;
+    int* d_status = nullptr;
+};
+
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 32, UK = 16;
+constexpr int NTHREADS = 192;
+constexpr int A_TILE_BYTES = TM * TK * 2;   // one term
+constexpr int B_TILE_BYTES = TN * TK * 2;
+constexpr int TMEM_COLS = 512;        // two 128 x 256 FP32 accumulators
+constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
+
+template <int T> struct Cfg {
+    static constexpr int NS = T == 3 ? 3 : 4;
+    static constexpr int STAGE_BYTES = T * (A_TILE_BYTES + B_TILE_BYTES);
+    static constexpr int BAR_OFF = NS * STAGE_BYTES;
+    static constexpr int SMEM = BAR_OFF + 256;
+};
+
+struct GemmArgs {
+    const unsigned char* planes;   // term t plane at planes + t * plane_bytes
+    long long plane_bytes;
+    const SplitProb* probs;
+    const int4* tiles;
+    const float* B;
+    float* O;
+    int C;                          // valid columns (2F)
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-void split_tables_destroy(sht_plan_s* p) { delete p->split; p->split = nullptr; }
-cudaError_t launch_legendre_fwd_split(const sht_plan_s*, const void*, void*, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
-cudaError_t launch_legendre_inv_split(const sht_plan_s*, const void*, void*, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed, false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// (K-direction core stride) and stride (M/N-direction 8-row-group stride)
+// byte offsets, descriptor version 1 at bit 46.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B,
+// both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b,
+                                         uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int T>
+__global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
+    using CF = Cfg<T>;
+    constexpr int NS = CF::NS;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
+    // bars: full_a[NS], full_b[NS], empty[NS], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1));
+    volatile int* abort_flag =
+        reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1) + 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 tile = g.tiles[blockIdx.x];
+    const SplitProb pr = g.probs[tile.x];
+    const int mt = tile.y, ct = tile.z;
+    const int nkt = pr.nkt;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_a = [&](int s) { return bar0 + 8u * s; };
+    auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
+    auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
+    const uint32_t done = bar0 + 8u * (3 * NS);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full_a(s), 1);
+            mbar_init(full_b(s), 128);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
+    if (warp == 4) {
+        // ---- producer of A: one bulk copy per term per stage ----
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)h * TK * 2;
+            for (int it = 0; it < nkt; ++it) {
+                const int s = it % NS;
+                const uint32_t ph = (uint32_t)(it / NS) & 1u;
+                if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+                mbar_expect_tx(full_a(s), bytes * T);
+                const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
+                                          (long long)mt * TM * TK * 2;
+                unsigned char* st = smem + s * CF::STAGE_BYTES;
+                for (int t = 0; t < T; ++t)
+                    bulk_g2s(smem_u32(st + t * A_TILE_BYTES),
+                             g.planes + (long long)t * g.plane_bytes + src_off, bytes,
+                             full_a(s));
+            }
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            bool ok = true;
+            for (int it = 0; it < nkt && ok; ++it) {
+                const int s = it % NS;
+                const uint32_t ph = (uint32_t)(it / NS) & 1u;
+                ok = mbar_wait(full_a(s), ph, abort_flag) && mbar_wait(full_b(s), ph, abort_flag);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = smem_u32(smem + s * CF::STAGE_BYTES);
+                const uint32_t bst = st + T * A_TILE_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < TK / UK; ++ks) {
+#pragma unroll
+                    for (int a = 0; a < T; ++a) {
+#pragma unroll
+                        for (int b = 0; b < T - a; ++b) {
+                            const uint64_t ad = sdesc(st + a * A_TILE_BYTES + ks * 256, 128, 512);
+                            const uint64_t bd = sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, 512);
+                            // (0,0) -> leading accumulator; the first of the
+                            // others, (0,1), opens the correction accumulator
+                            const bool lead = (a == 0 && b == 0);
+                            const uint32_t acc =
+                                (it > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
+                            mma_bf16(lead ? tmem : tmem + TN, ad, bd, acc);
+                        }
+                    }
+                }
+                mma_commit(empty(s));
+            }
+            // done fires once every MMA issued so far has completed
+            mma_commit(done);
+        }
+    } else {
+        // ---- converters: B (FP32, rows k, columns c) -> T BF16 K-major tiles ----
+        const int tid = threadIdx.x;   // 0..127
+        const int cbase = ct * TN;
+        for (int it = 0; it < nkt; ++it) {
+            const int s = it % NS;
+            const uint32_t ph = (uint32_t)(it / NS) & 1u;
+            if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+            unsigned char* bst = smem + s * CF::STAGE_BYTES + T * A_TILE_BYTES;
+            const int k0 = it * TK;
+#pragma unroll 2
+            for (int v = 0; v < (TN * TK / 8) / 128; ++v) {
+                const int u = tid + 128 * v;
+                const int c = u & (TN - 1);
+                const int k8 = u >> 8;
+                const int cg = cbase + c;
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int k = k0 + k8 * 8 + e;
+                    x[e] = (k < pr.K && cg < g.C)
+                               ? __ldg(g.B + pr.b_off + (long long)k * pr.b_stride + cg)
+                               : 0.f;
+                }
+                const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    float y[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(x[e]);
+                        y[e] = __bfloat162float(hb);
+                        x[e] -= y[e];
+                    }
+                    uint4 pk;
+                    pk.x = pack_bf16(y[0], y[1]);
+                    pk.y = pack_bf16(y[2], y[3]);
+                    pk.z = pack_bf16(y[4], y[5]);
+                    pk.w = pack_bf16(y[6], y[7]);
+                    *reinterpret_cast<uint4*>(bst + t * B_TILE_BYTES + off) = pk;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full_b(s));
+        }
+        // ---- epilogue: TMEM lanes 32*warp .. +31 = tile rows ----
+        const bool have = nkt > 0;
+        bool ok = true;
+        if (have) ok = mbar_wait(done, 0, abort_flag);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = TM * mt + 32 * warp + lane;
+        const bool row_ok = row < pr.Mrows && ok && !*abort_flag;
+        float* orow = g.O + pr.o_off + (long long)row * pr.o_stride;
+        const bool vec = ((pr.o_stride & 3) == 0) && ((pr.o_off & 3) == 0) &&
+                         ((g.C & 3) == 0);
+        for (int ch = 0; ch < TN / 16; ++ch) {
+            uint32_t r[16];
+            if (have && ok) {
+                uint32_t r2[16];
+                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ch * 16);
+                tmem_ld16(ta, r);
+                tmem_ld16(ta + TN, r2);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    r[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(r2[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) r[i] = 0u;
+            }
+            const int c0 = cbase + ch * 16;
+            if (!row_ok || c0 >= g.C) continue;
+            if (vec && c0 + 16 <= g.C) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float4 f;
+                    f.x = __uint_as_float(r[4 * i + 0]);
+                    f.y = __uint_as_float(r[4 * i + 1]);
+                    f.z = __uint_as_float(r[4 * i + 2]);
+                    f.w = __uint_as_float(r[4 * i + 3]);
+                    *reinterpret_cast<float4*>(orow + c0 + 4 * i) = f;
+                }
+            } else {
+                for (int i = 0; i < 16 && c0 + i < g.C; ++i) orow[c0 + i] = __uint_as_float(r[i]);
+            }
+        }
+    }
+    if (*abort_flag && threadIdx.x == 0) atomicOr(g.status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        // MMAs still in flight after an abort must finish before the
+        // accumulator is released (bounded as well).
+        if (*abort_flag && nkt > 0) {
+            const long long t0 = clock64();
+            while (!mbar_try(done, 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Split the FP64 P~ table into T BF16 planes, pre-tiled (see top of file).
+// One block per (m, parity) problem.  fwd: A rows are the parity rows n_r,
+// K the northern nodes; inv: A rows are the nodes, K the parity rows.
+__global__ void split_table_kernel(const double* __restrict__ pnm, int ldp, int N, int Jh,
+                                   const SplitProb* __restrict__ probs, int inverse, int T,
+                                   unsigned char* planes, long long plane_bytes) {
+    const int p = blockIdx.x;
+    const int m = p >> 1, q = p & 1;
+    const SplitProb pr = probs[p];
+    const size_t row0 = coef_offset(N, m) + q;
+    const long long K32 = (long long)pr.nkt * TK;
+    const long long n_el = (long long)pr.R8 * K32;
+    for (long long e = threadIdx.x; e < n_el; e += blockDim.x) {
+        const int r = (int)(e / K32);
+        const int k = (int)(e % K32);
+        double v = 0.0;
+        if (!inverse) {
+            if (r < pr.Mrows && k < Jh) v = pnm[(row0 + 2 * (size_t)r) * ldp + k];
+        } else {
+            if (r < Jh && k < pr.K) v = pnm[(row0 + 2 * (size_t)k) * ldp + r];
+        }
+        const int kt = k / TK, kk = k % TK;
+        const long long off = pr.a_off + (long long)kt * pr.R8 * TK * 2 +
+                              (long long)(((r >> 3) * (TK / 8) + (kk >> 3)) * 128 +
+                                          (r & 7) * 16 + (kk & 7) * 2);
+        for (int t = 0; t < T; ++t) {
+            const __nv_bfloat16 hb = __float2bfloat16_rn((float)v);
+            *reinterpret_cast<__nv_bfloat16*>(planes + t * plane_bytes + off) = hb;
+            v -= (double)__bfloat162float(hb);
+        }
+    }
+}
+
+int terms_of(int prec) { return (prec == SHT_BF16X2 || prec == SHT_FP16X2) ? 2 : 3; }
+
+cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* O,
+                        cudaStream_t s) {
+    const SplitTables* st = p->split;
+    GemmArgs g;
+    g.planes = inverse ? st->inv_planes : st->fwd_planes;
+    g.plane_bytes = (long long)(inverse ? st->inv_plane_bytes : st->fwd_plane_bytes);
+    g.probs = inverse ? st->d_probs_inv : st->d_probs_fwd;
+    g.tiles = inverse ? st->d_tiles_inv : st->d_tiles_fwd;
+    g.B = static_cast<const float*>(B);
+    g.O = static_cast<float*>(O);
+    g.C = 2 * p->F;
+    g.status = st->d_status;
+    const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
+    if (ntiles == 0) return cudaSuccess;
+    if (st->terms == 3) {
+        cudaFuncSetAttribute(split_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<3>::SMEM);
+        split_gemm_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(g);
+    } else {
+        cudaFuncSetAttribute(split_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<2>::SMEM);
+        split_gemm_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
+    if (p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3) {
+        set_error("FP16 split plans are not available in this build (BF16 only)");
+        return cudaErrorNotSupported;
+    }
+    SplitTables* st = new (std::nothrow) SplitTables();
+    if (!st) return cudaErrorMemoryAllocation;
+    p->split = st;
+    st->terms = terms_of(p->prec);
+    const int N = p->N, Jh = p->Jh, C = 2 * p->F;
+    const int nprob = 2 * (N + 1);
+    std::vector<SplitProb> pf(nprob), pi(nprob);
+    std::vector<int4> tf, ti;
+    long long fwd_bytes = 0, inv_bytes = 0;
+    const int nct = (C + TN - 1) / TN;
+    for (int m = 0; m <= N; ++m) {
+        for (int q = 0; q < 2; ++q) {
+            const int d = N - m - q;
+            const int R = d >= 0 ? d / 2 + 1 : 0;
+            const long long row0 = (long long)coef_offset(N, m) + q;
+            SplitProb& f = pf[2 * m + q];
+            f.a_off = fwd_bytes;
+            f.R8 = (R + 7) / 8 * 8;
+            f.Mrows = R;
+            f.K = Jh;
+            f.nkt = (Jh + TK - 1) / TK;
+            f.b_off = (long long)(2 * m + q) * Jh * C;
+            f.b_stride = C;
+            f.o_off = row0 * C;
+            f.o_stride = 2 * C;
+            fwd_bytes += (long long)f.R8 * f.nkt * TK * 2;
+            for (int mt = 0; mt * TM < R; ++mt)
+                for (int c = 0; c < nct; ++c) tf.push_back(make_int4(2 * m + q, mt, c, 0));
+            SplitProb& v = pi[2 * m + q];
+            v.a_off = inv_bytes;
+            v.R8 = (Jh + 7) / 8 * 8;
+            v.Mrows = Jh;
+            v.K = R;
+            v.nkt = (R + TK - 1) / TK;
+            v.b_off = row0 * C;
+            v.b_stride = 2 * C;
+            v.o_off = (long long)(2 * m + q) * Jh * C;
+            v.o_stride = C;
+            inv_bytes += (long long)v.R8 * v.nkt * TK * 2;
+            for (int mt = 0; mt * TM < Jh; ++mt)
+                for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, 0));
+        }
+    }
+    st->fwd_plane_bytes = (size_t)(fwd_bytes + 255) / 256 * 256;
+    st->inv_plane_bytes = (size_t)(inv_bytes + 255) / 256 * 256;
+    st->ntiles_fwd = (int)tf.size();
+    st->ntiles_inv = (int)ti.size();
+    cudaError_t e;
+    if ((e = cudaMalloc(&st->fwd_planes, st->fwd_plane_bytes * st->terms + 256)) != cudaSuccess ||
+        (e = cudaMalloc(&st->inv_planes, st->inv_plane_bytes * st->terms + 256)) != cudaSuccess ||
+        (e = cudaMalloc(&st->d_probs_fwd, nprob * sizeof(SplitProb))) != cudaSuccess ||
+        (e = cudaMalloc(&st->d_probs_inv, nprob * sizeof(SplitProb))) != cudaSuccess ||
+        (e = cudaMalloc(&st->d_tiles_fwd, (tf.size() + 1) * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&st->d_tiles_inv, (ti.size() + 1) * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc(&st->d_status, sizeof(int))) != cudaSuccess) {
+        set_error("split tables: %s", cudaGetErrorString(e));
+        return e;
+    }
+    // rows of A beyond R8 inside a 128-row tile are never copied; zero the
+    // planes so K padding and row padding read as zero
+    if ((e = cudaMemsetAsync(st->fwd_planes, 0, st->fwd_plane_bytes * st->terms, s)) ||
+        (e = cudaMemsetAsync(st->inv_planes, 0, st->inv_plane_bytes * st->terms, s)) ||
+        (e = cudaMemsetAsync(st->d_status, 0, sizeof(int), s)) ||
+        (e = cudaMemcpyAsync(st->d_probs_fwd, pf.data(), nprob * sizeof(SplitProb),
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(st->d_probs_inv, pi.data(), nprob * sizeof(SplitProb),
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(st->d_tiles_fwd, tf.data(), tf.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, s)) ||
+        (e = cudaMemcpyAsync(st->d_tiles_inv, ti.data(), ti.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, s)))
+        return e;
+    split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_fwd, 0,
+                                            st->terms, st->fwd_planes,
+                                            (long long)st->fwd_plane_bytes);
+    split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_inv, 1,
+                                            st->terms, st->inv_planes,
+                                            (long long)st->inv_plane_bytes);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);   // host vectors above must outlive the copies
+}
+
+void split_tables_destroy(sht_plan_s* p) {
+    SplitTables* st = p->split;
+    if (!st) return;
+    void* ptrs[] = {st->fwd_planes, st->inv_planes, st->d_probs_fwd, st->d_probs_inv,
+                    st->d_tiles_fwd, st->d_tiles_inv, st->d_status};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete st;
+    p->split = nullptr;
+}
+
+cudaError_t launch_legendre_fwd_split(const sht_plan_s* p, const void* work, void* spec,
+                                      cudaStream_t s) {
+    return launch_gemm(p, false, work, spec, s);
+}
+
+cudaError_t launch_legendre_inv_split(const sht_plan_s* p, const void* spec, void* work,
+                                      cudaStream_t s) {
+    return launch_gemm(p, true, spec, work, s);
+}
+
+int split_status_read_and_clear(const sht_plan_s* p) {
+    if (!p->split || !p->split->d_status) return 0;
+    int v = 0;
+    if (cudaMemcpy(&v, p->split->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    if (v) cudaMemset(p->split->d_status, 0, sizeof(int));
+    return v;
 }
 
 }  // namespace sht

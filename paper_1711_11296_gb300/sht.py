@@ -121,6 +121,11 @@ class Plan:
                                        mu.ctypes.data_as(dp), pnm.ctypes.data_as(dp)))
         return w, mu, pnm
 
+    def status(self):
+        """Synchronise; raise SHTError if a kernel of this plan gave up on a
+        bounded wait since the last check."""
+        check(lib.sht_plan_status(self._h))
+
     def profile(self, on=True):
         """Turn per-launch event timing on or off."""
         check(lib.sht_profile_enable(self._h, 1 if on else 0))

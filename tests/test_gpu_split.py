@@ -1,0 +1,133 @@
+"""Split-precision path (FP32 FFT, BF16-split Legendre contractions on the
+tcgen05 tensor cores) against the FP64 oracle.
+
+The split path takes FP32 inputs, so the oracle is given the same FP32
+values (widened to FP64) and the error is that of the path itself.
+Tolerances (relative L2 over the whole output, per direction):
+  bf16x3: 1e-6  -- the accuracy target of the split path; three BF16 terms
+                   carry 24 significand bits (the FP32 input precision) and
+                   the tensor cores accumulate each K=16 block in FP32, so
+                   about sqrt(K/16) * 2^-24 ~ 4e-7 is expected at K = 641.
+  bf16x2: 5e-5  -- two BF16 terms carry 16 bits: ~2^-16 = 1.5e-5 per operand.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1711_11296_gb300 import workloads as W
+from sht_testutil import built_lib, rel_l2, to_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x3": 1e-6, "bf16x2": 5e-5}
+
+CASES = [
+    (31, 65, 128, 1),
+    (31, 65, 128, 7),
+    (0, 1, 2, 3),
+    (12, 31, 30, 4),
+    (40, 81, 96, 2),
+    (63, 129, 256, 19),
+    (159, 321, 640, 33),
+]
+
+
+@pytest.fixture(scope="module")
+def sht():
+    built_lib()
+    from paper_1711_11296_gb300 import sht as S
+    return S
+
+
+def _f32(a):
+    return np.asarray(a).astype(np.float32).astype(np.float64)
+
+
+def _c64(a):
+    return np.asarray(a).astype(np.complex64).astype(np.complex128)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("N,J,I,F", CASES)
+def test_split_forward_inverse_match_oracle(sht, prec, N, J, I, F):
+    p = sht.Plan(N, J, I, F, prec)
+    x = _f32(W.random_grid(F, J, I, seed=700 + N))
+    got = p.forward(to_cuda(x, torch.float32)).cpu().numpy()
+    ref = O.analysis(x, N)
+    assert rel_l2(got, ref) <= TOL[prec], rel_l2(got, ref)
+    assert np.all(got[:N + 1].imag == 0.0)
+    a = _c64(W.random_spectrum(N, F, "n^-1.5", seed=800 + N))
+    g = p.inverse(to_cuda(a, torch.complex64)).cpu().numpy()
+    gref = O.synthesis(a, N, J, I)
+    assert rel_l2(g, gref) <= TOL[prec], rel_l2(g, gref)
+    p.status()
+
+
+@pytest.mark.parametrize("N,J,I,F", [(31, 65, 128, 3), (63, 129, 256, 4)])
+def test_split_adjoints_and_restriction(sht, N, J, I, F):
+    p = sht.Plan(N, J, I, F, "bf16x3")
+    a = _c64(W.random_spectrum(N, F, "n^-1.5", seed=900 + N))
+    x = _f32(W.random_grid(F, J, I, seed=901 + N))
+    g0 = p.adjoint(0, to_cuda(a, torch.complex64)).cpu().numpy()
+    assert rel_l2(g0, O.adjoint_analysis(a, N, J, I)) <= 1e-6
+    g1 = p.adjoint(1, to_cuda(x, torch.float32)).cpu().numpy()
+    assert rel_l2(g1, O.adjoint_synthesis(x, N)) <= 1e-6
+    fine = _f32(W.random_grid(F, 2 * (J + 1) - 1, 2 * I, seed=902 + N))
+    got = p.restrict_nested(to_cuda(fine, torch.float32), 1).cpu().numpy()
+    assert rel_l2(got, O.restrict_nested(fine, 1, N)) <= 1e-6
+    p.status()
+
+
+def test_split_t319_errors_per_field(sht):
+    """T319 x 300 field-levels: per-field spectral and grid errors of both
+    BF16 splits against the oracle on sampled fields (all fields run on the
+    GPU).  Writes the table to $SHT_REPORT_DIR if set."""
+    w = W.WORKLOADS["T319"]
+    fields = [0, 1, 99, 150, 299]
+    x = np.stack([W.random_grid_field(f, w.J, w.I) for f in range(w.F)])
+    x = _f32(x)
+    a = _c64(W.workload_spectrum(w))
+    ref_s = O.analysis(x[fields], w.N)
+    ref_g = O.synthesis(a[:, fields], w.N, w.J, w.I)
+    report = {}
+    for prec in ("bf16x3", "bf16x2"):
+        p = sht.Plan(w.N, w.J, w.I, w.F, prec)
+        s = p.forward(to_cuda(x, torch.float32)).cpu().numpy()[:, fields]
+        g = p.inverse(to_cuda(a, torch.complex64)).cpu().numpy()[fields]
+        p.status()
+        es = [rel_l2(s[:, k], ref_s[:, k]) for k in range(len(fields))]
+        eg = [rel_l2(g[k], ref_g[k]) for k in range(len(fields))]
+        report[prec] = {"fields": fields, "spectral_rel_l2": es, "grid_rel_l2": eg}
+        assert max(es) <= TOL[prec] and max(eg) <= TOL[prec], (prec, es, eg)
+        del p
+    out = os.environ.get("SHT_REPORT_DIR")
+    if out:
+        with open(os.path.join(out, "split_errors_T319.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
+
+
+def test_split_t639_sampled(sht):
+    w = W.WORKLOADS["T639"]
+    p = sht.Plan(w.N, w.J, w.I, w.F, "bf16x3")
+    fields = [0, 77, 255]
+    ms = [0, 1, 2, 320, 638, 639]
+    x = _f32(np.stack([W.random_grid_field(f, w.J, w.I) for f in range(w.F)]))
+    got = p.forward(to_cuda(x, torch.float32)).cpu().numpy()
+    ref = O.analysis(x[fields], w.N, ms=ms)
+    num = den = 0.0
+    for m in ms:
+        r0 = O.coef_offset(w.N, m)
+        d = got[r0:r0 + w.N - m + 1][:, fields] - ref[m]
+        num += np.sum(np.abs(d) ** 2)
+        den += np.sum(np.abs(ref[m]) ** 2)
+    assert np.sqrt(num / den) <= 1e-6, np.sqrt(num / den)
+    a = _c64(W.workload_spectrum(w))
+    grid = p.inverse(to_cuda(a, torch.complex64)).cpu().numpy()
+    rows = [1, 2, 640, 641, 1281]
+    gref = O.synthesis_rows(a[:, fields], w.N, w.J, w.I, rows)
+    assert rel_l2(grid[fields][:, np.array(rows) - 1, :], gref) <= 1e-6
+    p.status()
