@@ -149,9 +149,10 @@ int sht_forward_noalloc(int N, int J, int I, int nfields, const double* grid,
                         double* spec, void* stream);
 
 /* Synchronise the plan's device and report device-side failures of the
- * plan's kernels since the last call: SHT_ERR_TIMEOUT if a tensor-core
- * kernel gave up on one of its bounded waits (its outputs are then
- * invalid), SHT_OK otherwise.  Clears the recorded status. */
+ * plan's kernels since the last call: SHT_ERR_TIMEOUT if a kernel gave
+ * up on one of its bounded waits (a tensor-core pipeline stage or an
+ * asynchronous copy; that call's outputs are then invalid), SHT_OK
+ * otherwise.  Clears the recorded status. */
 int sht_plan_status(sht_plan_t plan);
 
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer

@@ -60,6 +60,7 @@ bool factor_fft(int L, FftShape& sh) {
         sh.span[q] = span;
     }
     sh.npass = np;
+    fft_shape_offsets(sh);
     return true;
 }
 
@@ -70,8 +71,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 void free_plan_memory(sht_plan_s* p) {
     void* ptrs[] = {p->d_mu, p->d_sin, p->d_w, p->d_w_over_I, p->d_eps, p->d_amm,
-                    p->d_pnm, p->d_rev, p->d_tw, p->d_twpost, p->d_work,
-                    p->d_tiles_fwd, p->d_tiles_inv};
+                    p->d_pnm, p->d_rev, p->d_tw, p->d_twpost, p->d_twpass, p->d_work,
+                    p->d_tiles_fwd, p->d_tiles_inv, p->d_status};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->split) split_tables_destroy(p);
@@ -187,7 +188,7 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
     p->fft = shape;
     const bool fp64 = precision == SHT_FP64;
     const size_t vbytes = fp64 ? sizeof(double2) : sizeof(float2);
-    const size_t rowbytes = (size_t)shape.L * vbytes;
+    const size_t rowbytes = (size_t)fft_row_pitch(shape.L, fp64) * vbytes;
     const size_t budget = 110 * 1024;
     long g = (long)((budget / rowbytes > 1 ? budget / rowbytes - 1 : 0) / 2);
     if (g < 1) g = 1;
@@ -232,12 +233,16 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
               alloc((void**)&p->d_rev, L * sizeof(int), "FFT") &&
               alloc(&p->d_tw, L * vbytes, "FFT") &&
               alloc(&p->d_twpost, L * vbytes, "FFT") &&
+              alloc(&p->d_twpass, (shape.twtotal + 1) * vbytes, "FFT") &&
               alloc(&p->d_work, p->work_bytes, "workspace") &&
               alloc((void**)&p->d_tiles_fwd, tf.size() * sizeof(int4), "tiles") &&
-              alloc((void**)&p->d_tiles_inv, ti.size() * sizeof(int4), "tiles");
+              alloc((void**)&p->d_tiles_inv, ti.size() * sizeof(int4), "tiles") &&
+              alloc((void**)&p->d_status, sizeof(int), "status");
     if (ok) {
-        e = cudaMemcpy(p->d_tiles_fwd, tf.data(), tf.size() * sizeof(int4),
-                       cudaMemcpyHostToDevice);
+        e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_tiles_fwd, tf.data(), tf.size() * sizeof(int4),
+                           cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(p->d_tiles_inv, ti.data(), ti.size() * sizeof(int4),
                            cudaMemcpyHostToDevice);
@@ -492,7 +497,8 @@ extern "C" int sht_plan_status(sht_plan_t p) {
     const int v = split_status_read_and_clear(p);
     if (v < 0) return cuda_fail(cudaGetLastError(), "status read");
     if (v) {
-        set_error("a tensor-core kernel gave up waiting (bounded wait expired)");
+        set_error("a kernel gave up on a bounded wait (status bits %d: 1 tensor-core "
+                  "pipeline, 2 FFT copy)", v);
         return SHT_ERR_TIMEOUT;
     }
     return SHT_OK;

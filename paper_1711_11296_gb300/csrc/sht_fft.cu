@@ -5,7 +5,7 @@
 // A row of I real samples x_i is read as L = I/2 complex values
 // z_k = x_{2k} + i x_{2k+1}; an in-place mixed-radix (2/3/4/5) decimation-in-
 // frequency FFT of length L runs in shared memory and leaves Z in
-// digit-reversed order (rev[k] = position of frequency k).  The real
+// digit-reversed order (rev(k) = position of frequency k).  The real
 // spectrum follows from
 //   X_m = (Z_m + conj Z_{L-m})/2 + e^{-2 pi i m/I} (Z_m - conj Z_{L-m})/(2i).
 // The inverse builds Z_q = (Y_q + conj Y_{L-q}) + i e^{+2 pi i q/I} (Y_q - conj Y_{L-q})
@@ -14,12 +14,28 @@
 // x_{2k+1} = Im z_k.
 //
 // One CTA owns latitude pair (j, J-1-j) (0-based; the Equator row alone)
-// for G consecutive fields: 2G rows of L complex values plus the twiddle
-// table in shared memory.
+// for G consecutive fields: 2G rows of L complex values plus the per-pass
+// twiddle tables in shared memory.  Rows use the padded layout of
+// PadShift (element pos at pos + (pos >> s), odd row pitch), which keeps the
+// passes' power-of-two strides, the digit-reversed accesses and the
+// row-to-row distance off a single bank; each pass reads its twiddles from
+// a table contiguous in the butterfly index.  Global loads are issued eight
+// per thread before their stores so that their latencies overlap.  The
+// CTAs of all field groups of one latitude are adjacent in the launch
+// order, so their partial-sector writes of the same workspace rows meet in
+// L2.
+//
+// The half-lengths of the standard grids (64 ... 1280) have kernels
+// specialised at compile time: radices, spans, twiddle offsets and the
+// digit reversal are constants, so the index arithmetic needs no integer
+// division by a runtime value.  Other lengths use the same code with the
+// shape read at run time.
 #include "sht_internal.h"
 
 namespace sht {
 namespace {
+
+constexpr int NT = 256;   // threads per FFT CTA
 
 template <typename T> struct C2 {
     using V = typename Vec2<T>::type;
@@ -37,18 +53,216 @@ template <typename T> struct C2 {
     static __device__ __forceinline__ V mul_pi(V a) { return make(-a.y, a.x); }
 };
 
+// Compile-time factorisation; the same rule as the plan's (4s, 2s, 3s, 5s).
+struct Fac {
+    int L = 0, npass = 0, twtotal = 0;
+    int radix[kMaxRadixPasses] = {0};
+    int span[kMaxRadixPasses] = {0};
+    int twoff[kMaxRadixPasses] = {0};
+};
+
+constexpr Fac make_fac(int L) {
+    Fac f{};
+    f.L = L;
+    int rest = L, np = 0;
+    const int cand[4] = {4, 2, 3, 5};
+    for (int c = 0; c < 4; ++c)
+        while (rest % cand[c] == 0 && np < kMaxRadixPasses) {
+            f.radix[np++] = cand[c];
+            rest /= cand[c];
+        }
+    int span = L, off = 0;
+    for (int q = 0; q < np; ++q) {
+        span /= f.radix[q];
+        f.span[q] = span;
+        f.twoff[q] = off;
+        off += (f.radix[q] - 1) * span;
+    }
+    f.npass = np;
+    f.twtotal = off;
+    return f;
+}
+
+template <int L> struct FacOf {
+    static constexpr Fac v = make_fac(L);
+};
+
+template <typename T>
+__device__ __forceinline__ int ph(int pos) {
+    return pos + (pos >> PadShift<T>::value);
+}
+
+// ---- radix-R DFTs (forward sign) ---------------------------------------
+template <typename T, int R> struct Dft;
+
+template <typename T> struct Dft<T, 2> {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ void run(V* a) {
+        using K = C2<T>;
+        const V y0 = K::add(a[0], a[1]);
+        a[1] = K::sub(a[0], a[1]);
+        a[0] = y0;
+    }
+};
+
+template <typename T> struct Dft<T, 3> {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ void run(V* a) {
+        using K = C2<T>;
+        const T h = (T)0.86602540378443864676;   // sin(2 pi/3)
+        const V t1 = K::add(a[1], a[2]), t2 = K::sub(a[1], a[2]);
+        const V y0 = K::add(a[0], t1);
+        const V m0 = K::make(a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y);
+        const V q = K::mul_mi(K::scale(t2, h));
+        a[0] = y0;
+        a[1] = K::add(m0, q);
+        a[2] = K::sub(m0, q);
+    }
+};
+
+template <typename T> struct Dft<T, 4> {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ void run(V* a) {
+        using K = C2<T>;
+        const V s02 = K::add(a[0], a[2]), d02 = K::sub(a[0], a[2]);
+        const V s13 = K::add(a[1], a[3]), d13 = K::mul_mi(K::sub(a[1], a[3]));
+        a[0] = K::add(s02, s13);
+        a[2] = K::sub(s02, s13);
+        a[1] = K::add(d02, d13);
+        a[3] = K::sub(d02, d13);
+    }
+};
+
+template <typename T> struct Dft<T, 5> {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ void run(V* a) {
+        using K = C2<T>;
+        // cos/sin of 2 pi/5 and 4 pi/5
+        const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+        const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+        const V b1 = K::add(a[1], a[4]), d1 = K::sub(a[1], a[4]);
+        const V b2 = K::add(a[2], a[3]), d2 = K::sub(a[2], a[3]);
+        const V y0 = K::add(a[0], K::add(b1, b2));
+        const V p1 = K::make(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
+        const V p2 = K::make(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
+        // q1 = s1 d1 + s2 d2, q2 = s2 d1 - s1 d2; y1 = p1 - i q1, y4 = p1 + i q1,
+        // y2 = p2 - i q2, y3 = p2 + i q2
+        const V q1 = K::make(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+        const V q2 = K::make(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+        a[0] = y0;
+        a[1] = K::add(p1, K::mul_mi(q1));
+        a[4] = K::sub(p1, K::mul_mi(q1));
+        a[2] = K::add(p2, K::mul_mi(q2));
+        a[3] = K::sub(p2, K::mul_mi(q2));
+    }
+};
+
+// One DIF butterfly of radix R: reads z[base + t M], t < R, applies the
+// radix-R DFT, multiplies output k1 by W_S^{n1 k1} (per-pass table entry
+// (k1 - 1) M + n1) and writes it back to z[base + k1 M].
+template <typename T, int R>
+__device__ __forceinline__ void bfly(typename Vec2<T>::type* z, int base, int M,
+                                     const typename Vec2<T>::type* tw, int n1) {
+    using V = typename Vec2<T>::type;
+    using K = C2<T>;
+    V a[R];
+    int id[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        id[t] = ph<T>(base + t * M);
+        a[t] = z[id[t]];
+    }
+    Dft<T, R>::run(a);
+    if (n1 != 0) {
+#pragma unroll
+        for (int k1 = 1; k1 < R; ++k1) a[k1] = K::mul(a[k1], tw[(k1 - 1) * M + n1]);
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) z[id[t]] = a[t];
+}
+
+// In-place mixed-radix DIF FFT over `nrows` padded rows (pitch LP), shape
+// known at run time.
+template <typename T>
+__device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
+                               const FftShape& sh, const typename Vec2<T>::type* twp) {
+    const int L = sh.L;
+    for (int p = 0; p < sh.npass; ++p) {
+        const int r = sh.radix[p];
+        const int M = sh.span[p];
+        const int S = r * M;
+        const int nb = L / r;
+        const int total = nrows * nb;
+        const typename Vec2<T>::type* tw = twp + sh.twoff[p];
+        for (int idx = threadIdx.x; idx < total; idx += NT) {
+            const int row = idx / nb;
+            const int b = idx - row * nb;
+            const int blk = b / M;
+            const int n1 = b - blk * M;
+            auto* z = rows + (size_t)row * LP;
+            const int base = blk * S + n1;
+            if (r == 4)
+                bfly<T, 4>(z, base, M, tw, n1);
+            else if (r == 2)
+                bfly<T, 2>(z, base, M, tw, n1);
+            else if (r == 5)
+                bfly<T, 5>(z, base, M, tw, n1);
+            else
+                bfly<T, 3>(z, base, M, tw, n1);
+        }
+        __syncthreads();
+    }
+}
+
+// The same with the shape a compile-time constant (pass P onwards).
+template <typename T, int L, int P>
+__device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int nrows, int LP,
+                                             const typename Vec2<T>::type* twp) {
+    constexpr Fac F = FacOf<L>::v;
+    if constexpr (P < F.npass) {
+        constexpr int R = F.radix[P];
+        constexpr int M = F.span[P];
+        constexpr int S = R * M;
+        constexpr int NB = L / R;
+        constexpr int OFF = F.twoff[P];
+        const int total = nrows * NB;
+        for (int idx = threadIdx.x; idx < total; idx += NT) {
+            const int row = idx / NB;
+            const int b = idx - row * NB;
+            const int blk = b / M;
+            const int n1 = b - blk * M;
+            bfly<T, R>(rows + (size_t)row * LP, blk * S + n1, M, twp + OFF, n1);
+        }
+        __syncthreads();
+        passes_fixed<T, L, P + 1>(rows, nrows, LP, twp);
+    }
+}
+
+// Digit-reversed position of frequency k.
+template <int L>
+__device__ __forceinline__ int rev_fixed(int k) {
+    constexpr Fac F = FacOf<L>::v;
+    int pos = 0;
+#pragma unroll
+    for (int q = 0; q < F.npass; ++q) {
+        pos += (k % F.radix[q]) * F.span[q];
+        k /= F.radix[q];
+    }
+    return pos;
+}
+
 template <typename T>
 struct FwdArgs {
     using V = typename Vec2<T>::type;
     const T* grid;
     RowSource src;
     V* work;
-    const V* tw;
+    const V* twp;      // per-pass twiddle tables
     const V* twpost;
     const int* rev;
     const double* rowscale;
     double mscale0, mscale1;
-    int F, J, Jh, L, N, G;
+    int F, J, Jh, L, LP, N, G;
     FftShape shape;
 };
 
@@ -57,167 +271,133 @@ struct InvArgs {
     using V = typename Vec2<T>::type;
     const V* work;
     T* grid;
-    const V* tw;
+    const V* twp;
     const V* twpost;
     const int* rev;
     const double* rowscale;
     double mfactor1;
-    int F, J, Jh, I, L, N, G;
+    int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
 
-// In-place mixed-radix DIF FFT (forward sign) over `nrows` rows of length L
-// held in shared memory.  Pass p: blocks of S = r M, butterfly (blk, n1)
-// reads z[blk S + n1 + M t], t < r, applies the radix-r DFT, multiplies
-// output k1 by W_S^{n1 k1} = W_L^{n1 k1 L/S}, and writes it to
-// z[blk S + n1 + M k1].
-template <typename T>
-__device__ void fft_rows_inplace(typename Vec2<T>::type* rows, int nrows, int L,
-                                 const FftShape& sh,
-                                 const typename Vec2<T>::type* tws) {
-    using V = typename Vec2<T>::type;
-    using K = C2<T>;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int p = 0; p < sh.npass; ++p) {
-        const int r = sh.radix[p];
-        const int M = sh.span[p];
-        const int S = r * M;
-        const int tws_step = L / S;
-        const int nb = L / r;
-        const int total = nrows * nb;
-        for (int idx = tid; idx < total; idx += nthr) {
-            const int row = idx / nb;
-            const int b = idx - row * nb;
-            const int blk = b / M;
-            const int n1 = b - blk * M;
-            V* z = rows + (size_t)row * L + blk * S + n1;
-            const int te = n1 * tws_step;   // twiddle exponent step for k1 = 1
-            if (r == 4) {
-                V a0 = z[0], a1 = z[M], a2 = z[2 * M], a3 = z[3 * M];
-                V s02 = K::add(a0, a2), d02 = K::sub(a0, a2);
-                V s13 = K::add(a1, a3), d13 = K::mul_mi(K::sub(a1, a3));
-                V y0 = K::add(s02, s13);
-                V y2 = K::sub(s02, s13);
-                V y1 = K::add(d02, d13);
-                V y3 = K::sub(d02, d13);
-                z[0] = y0;
-                if (te == 0) {
-                    z[M] = y1; z[2 * M] = y2; z[3 * M] = y3;
-                } else {
-                    z[M] = K::mul(y1, tws[te]);
-                    z[2 * M] = K::mul(y2, tws[2 * te]);
-                    z[3 * M] = K::mul(y3, tws[3 * te]);
-                }
-            } else if (r == 2) {
-                V a0 = z[0], a1 = z[M];
-                z[0] = K::add(a0, a1);
-                V y1 = K::sub(a0, a1);
-                z[M] = te == 0 ? y1 : K::mul(y1, tws[te]);
-            } else if (r == 5) {
-                // cos/sin of 2 pi/5 and 4 pi/5
-                const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
-                const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
-                V a0 = z[0], a1 = z[M], a2 = z[2 * M], a3 = z[3 * M], a4 = z[4 * M];
-                V b1 = K::add(a1, a4), d1 = K::sub(a1, a4);
-                V b2 = K::add(a2, a3), d2 = K::sub(a2, a3);
-                V y0 = K::add(a0, K::add(b1, b2));
-                V p1 = K::make(a0.x + c1 * b1.x + c2 * b2.x, a0.y + c1 * b1.y + c2 * b2.y);
-                V p2 = K::make(a0.x + c2 * b1.x + c1 * b2.x, a0.y + c2 * b1.y + c1 * b2.y);
-                // q1 = s1 d1 + s2 d2, q2 = s2 d1 - s1 d2; y1 = p1 - i q1, y4 = p1 + i q1,
-                // y2 = p2 - i q2, y3 = p2 + i q2
-                V q1 = K::make(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
-                V q2 = K::make(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
-                V y1 = K::add(p1, K::mul_mi(q1));
-                V y4 = K::sub(p1, K::mul_mi(q1));
-                V y2 = K::add(p2, K::mul_mi(q2));
-                V y3 = K::sub(p2, K::mul_mi(q2));
-                z[0] = y0;
-                if (te == 0) {
-                    z[M] = y1; z[2 * M] = y2; z[3 * M] = y3; z[4 * M] = y4;
-                } else {
-                    z[M] = K::mul(y1, tws[te]);
-                    z[2 * M] = K::mul(y2, tws[2 * te]);
-                    z[3 * M] = K::mul(y3, tws[3 * te]);
-                    z[4 * M] = K::mul(y4, tws[4 * te]);
-                }
-            } else {   // r == 3
-                const T h = (T)0.86602540378443864676;   // sin(2 pi/3)
-                V a0 = z[0], a1 = z[M], a2 = z[2 * M];
-                V t1 = K::add(a1, a2), t2 = K::sub(a1, a2);
-                V y0 = K::add(a0, t1);
-                V m0 = K::make(a0.x - (T)0.5 * t1.x, a0.y - (T)0.5 * t1.y);
-                V q = K::mul_mi(K::scale(t2, h));
-                V y1 = K::add(m0, q);
-                V y2 = K::sub(m0, q);
-                z[0] = y0;
-                if (te == 0) {
-                    z[M] = y1; z[2 * M] = y2;
-                } else {
-                    z[M] = K::mul(y1, tws[te]);
-                    z[2 * M] = K::mul(y2, tws[2 * te]);
-                }
-            }
-        }
-        __syncthreads();
-    }
+// Copy the per-pass twiddle tables into shared memory.
+template <typename V>
+__device__ __forceinline__ void load_twiddles(V* dst, const V* src, int n) {
+    for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
 }
 
-template <typename T, bool STRIDED>
-__global__ void __launch_bounds__(256) fft_forward_kernel(FwdArgs<T> A) {
+template <typename T, int LT>
+__device__ __forceinline__ void run_passes(typename Vec2<T>::type* rows, int nrows, int LP,
+                                           const FftShape& sh,
+                                           const typename Vec2<T>::type* twp) {
+    if constexpr (LT > 0)
+        passes_fixed<T, LT, 0>(rows, nrows, LP, twp);
+    else
+        passes_runtime<T>(rows, nrows, LP, sh, twp);
+}
+
+template <int LT>
+__device__ __forceinline__ int rev_of(int k, const int* rev) {
+    if constexpr (LT > 0)
+        return rev_fixed<LT>(k);
+    else
+        return rev[k];
+}
+
+// Iterates idx = tid, tid + NT, ... as (major, minor) = (idx / d, idx % d)
+// without dividing inside the loop.
+struct Walk2 {
+    int major, minor, step_major, step_minor, d;
+    __device__ __forceinline__ Walk2(int start, int d_) : d(d_) {
+        major = start / d;
+        minor = start - major * d;
+        step_major = NT / d;
+        step_minor = NT - step_major * d;
+    }
+    __device__ __forceinline__ void next() {
+        major += step_major;
+        minor += step_minor;
+        if (minor >= d) {
+            minor -= d;
+            ++major;
+        }
+    }
+};
+
+template <typename T, int LT, bool STRIDED>
+__global__ void __launch_bounds__(NT) fft_forward_kernel(FwdArgs<T> A) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = A.L;
-    V* tws = reinterpret_cast<V*>(smem_raw);
-    V* rows = tws + L;
-    const int jh = blockIdx.x;
-    const int f0 = blockIdx.y * A.G;
+    const int L = LT > 0 ? LT : A.L;
+    const int LP = A.LP;
+    V* rows = reinterpret_cast<V*>(smem_raw);
+    V* tws = rows + (size_t)2 * A.G * LP;
+    const int jh = blockIdx.y;
+    const int f0 = blockIdx.x * A.G;
     const int nf = min(A.G, A.F - f0);
     const bool equator = (jh == A.Jh - 1);
     const int nrows = equator ? nf : 2 * nf;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-
-    for (int e = tid; e < L; e += nthr) tws[e] = A.tw[e];
-    for (int r = 0; r < nrows; ++r) {
-        const int f = f0 + (r % nf);
+    const int tid = threadIdx.x;
+    auto row_ptr = [&](int r) -> const T* {
+        const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
-        const T* x = A.grid + (long long)f * A.src.field_stride + A.src.row_offset +
-                     (long long)j * A.src.row_stride;
-        V* z = rows + (size_t)r * L;
-        if (!STRIDED) {
-            const V* xv = reinterpret_cast<const V*>(x);
-            for (int k = tid; k < L; k += nthr) z[k] = xv[k];
-        } else {
-            const int s = A.src.elem_stride;
-            for (int k = tid; k < L; k += nthr)
-                z[k] = K::make(x[(long long)(2 * k) * s], x[(long long)(2 * k + 1) * s]);
+        return A.grid + (long long)f * A.src.field_stride + A.src.row_offset +
+               (long long)j * A.src.row_stride;
+    };
+
+    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT>::v.twtotal : A.shape.twtotal);
+    {
+        // element k of row r goes to rows[r LP + ph(k)]; eight loads in flight
+        const int s = A.src.elem_stride;
+        Walk2 w(tid, L);   // (row, k)
+        while (w.major < nrows) {
+            V v[8];
+            int rr[8], kk[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                rr[u] = w.major;
+                kk[u] = w.minor;
+                if (w.major < nrows) {
+                    const T* x = row_ptr(w.major);
+                    if (!STRIDED)
+                        v[u] = reinterpret_cast<const V*>(x)[w.minor];
+                    else
+                        v[u] = K::make(x[(long long)(2 * w.minor) * s],
+                                       x[(long long)(2 * w.minor + 1) * s]);
+                }
+                w.next();
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (rr[u] < nrows) rows[(size_t)rr[u] * LP + ph<T>(kk[u])] = v[u];
         }
     }
     __syncthreads();
-    fft_rows_inplace<T>(rows, nrows, L, A.shape, tws);
+    run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
     const int nout = (A.N + 1) * nf;
     const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
-    for (int idx = tid; idx < nout; idx += nthr) {
-        const int m = idx / nf;
-        const int fl = idx - m * nf;
-        const int pm = A.rev[m];
-        const int pc = A.rev[(L - m) % L];
-        const V w = A.twpost[m];
+    for (Walk2 w(tid, nf); w.major * nf + w.minor < nout; w.next()) {
+        const int m = w.major;
+        const int fl = w.minor;
+        const int pm = ph<T>(rev_of<LT>(m, A.rev));
+        const int pc = ph<T>(rev_of<LT>(m == 0 ? 0 : L - m, A.rev));
+        const V wt = A.twpost[m];
         auto real_spec = [&](const V* z) -> V {
-            V zm = z[pm];
-            V zc = K::conj(z[pc]);
-            V e = K::add(zm, zc);                  // 2 E_m
-            V o = K::mul_mi(K::sub(zm, zc));       // 2 O_m
-            return K::add(e, K::mul(w, o));        // 2 X_m
+            const V zm = z[pm];
+            const V zc = K::conj(z[pc]);
+            const V e = K::add(zm, zc);                  // 2 E_m
+            const V o = K::mul_mi(K::sub(zm, zc));       // 2 O_m
+            return K::add(e, K::mul(wt, o));             // 2 X_m
         };
-        const V xn = real_spec(rows + (size_t)fl * L);
+        const V xn = real_spec(rows + (size_t)fl * LP);
         V S, Asym;
         if (equator) {
             S = xn;
             Asym = K::make((T)0, (T)0);
         } else {
-            const V xs = real_spec(rows + (size_t)(nf + fl) * L);
+            const V xs = real_spec(rows + (size_t)(nf + fl) * LP);
             S = K::add(xn, xs);
             Asym = K::sub(xn, xs);
         }
@@ -228,63 +408,73 @@ __global__ void __launch_bounds__(256) fft_forward_kernel(FwdArgs<T> A) {
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) fft_inverse_kernel(InvArgs<T> A) {
+template <typename T, int LT>
+__global__ void __launch_bounds__(NT) fft_inverse_kernel(InvArgs<T> A) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int L = A.L;
-    V* tws = reinterpret_cast<V*>(smem_raw);
-    V* rows = tws + L;
-    const int jh = blockIdx.x;
-    const int f0 = blockIdx.y * A.G;
+    const int L = LT > 0 ? LT : A.L;
+    const int LP = A.LP;
+    V* rows = reinterpret_cast<V*>(smem_raw);
+    V* tws = rows + (size_t)2 * A.G * LP;
+    const int jh = blockIdx.y;
+    const int f0 = blockIdx.x * A.G;
     const int nf = min(A.G, A.F - f0);
     const bool equator = (jh == A.Jh - 1);
     const int nrows = equator ? nf : 2 * nf;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x;
 
-    for (int e = tid; e < L; e += nthr) tws[e] = A.tw[e];
+    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT>::v.twtotal : A.shape.twtotal);
     // unfold S/A into the two hemispheres' zonal spectra Y_m, m <= N
+    // (four loads in flight per thread)
     const int nin = (A.N + 1) * nf;
-    for (int idx = tid; idx < nin; idx += nthr) {
-        const int m = idx / nf;
-        const int fl = idx - m * nf;
-        const size_t base = ((size_t)m * 2 * A.Jh + jh) * A.F + f0 + fl;
-        const V S = A.work[base];
-        const T fac = (T)(m == 0 ? 1.0 : A.mfactor1);
-        V yn, ys;
-        if (equator) {
-            yn = K::scale(S, fac);
-            ys = yn;
-        } else {
-            const V Asym = A.work[base + (size_t)A.Jh * A.F];
-            yn = K::scale(K::add(S, Asym), fac);
-            ys = K::scale(K::sub(S, Asym), fac);
+    {
+        Walk2 w(tid, nf);   // (m, field)
+        while (w.major * nf + w.minor < nin) {
+            V Sv[4], Av[4];
+            int mm[4], ff[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                mm[u] = w.major;
+                ff[u] = w.minor;
+                if (w.major * nf + w.minor < nin) {
+                    const size_t base = ((size_t)w.major * 2 * A.Jh + jh) * A.F + f0 + w.minor;
+                    Sv[u] = A.work[base];
+                    Av[u] = equator ? K::make((T)0, (T)0) : A.work[base + (size_t)A.Jh * A.F];
+                }
+                w.next();
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int m = mm[u], fl = ff[u];
+                if (m * nf + fl >= nin) continue;
+                const T fac = (T)(m == 0 ? 1.0 : A.mfactor1);
+                V yn = K::scale(K::add(Sv[u], Av[u]), fac);
+                V ys = K::scale(K::sub(Sv[u], Av[u]), fac);
+                if (m == 0) {
+                    yn.y = (T)0;
+                    ys.y = (T)0;
+                }
+                rows[(size_t)fl * LP + ph<T>(m)] = yn;
+                if (!equator) rows[(size_t)(nf + fl) * LP + ph<T>(m)] = ys;
+            }
         }
-        if (m == 0) {
-            yn.y = (T)0;
-            ys.y = (T)0;
-        }
-        rows[(size_t)fl * L + m] = yn;
-        if (!equator) rows[(size_t)(nf + fl) * L + m] = ys;
     }
     const int nz = L - (A.N + 1);
-    for (int idx = tid; idx < nrows * nz; idx += nthr) {
-        const int r = idx / nz;
-        const int q = A.N + 1 + (idx - r * nz);
-        rows[(size_t)r * L + q] = K::make((T)0, (T)0);
+    if (nz > 0) {
+        for (Walk2 w(tid, nz); w.major < nrows; w.next())
+            rows[(size_t)w.major * LP + ph<T>(A.N + 1 + w.minor)] = K::make((T)0, (T)0);
     }
     __syncthreads();
     // Hermitian packing into conj(Z), pairs (q, L-q) owned by one thread
     const int half = L / 2;
-    for (int idx = tid; idx < nrows * (half + 1); idx += nthr) {
-        const int r = idx / (half + 1);
-        const int q = idx - r * (half + 1);
+    for (Walk2 w(tid, half + 1); w.major < nrows; w.next()) {
+        const int q = w.minor;
         const int qc = L - q;
         if (q > qc) continue;
-        V* z = rows + (size_t)r * L;
-        const V yq = z[q];
-        const V yc = (q == 0) ? K::make((T)0, (T)0) : z[qc];
+        V* z = rows + (size_t)w.major * LP;
+        const V yq = z[ph<T>(q)];
+        const V yc = (q == 0) ? K::make((T)0, (T)0) : z[ph<T>(qc)];
         // Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q})
         const V wq = K::conj(A.twpost[q]);
         const V zq = K::add(K::add(yq, K::conj(yc)),
@@ -293,31 +483,62 @@ __global__ void __launch_bounds__(256) fft_inverse_kernel(InvArgs<T> A) {
             const V wc = K::conj(A.twpost[qc]);
             const V zc = K::add(K::add(yc, K::conj(yq)),
                                 K::mul_pi(K::mul(wc, K::sub(yc, K::conj(yq)))));
-            z[qc] = K::conj(zc);
+            z[ph<T>(qc)] = K::conj(zc);
         }
-        z[q] = K::conj(zq);
+        z[ph<T>(q)] = K::conj(zq);
     }
     __syncthreads();
-    fft_rows_inplace<T>(rows, nrows, L, A.shape, tws);
+    run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
     const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
-    for (int r = 0; r < nrows; ++r) {
-        const int f = f0 + (r % nf);
+    for (Walk2 w(tid, L); w.major < nrows; w.next()) {
+        const int r = w.major, k = w.minor;
+        const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
         V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I);
-        const V* z = rows + (size_t)r * L;
-        for (int k = tid; k < L; k += nthr) {
-            const V v = z[A.rev[k]];
-            xv[k] = K::make(v.x * rs, -v.y * rs);
-        }
+        const V v = rows[(size_t)r * LP + ph<T>(rev_of<LT>(k, A.rev))];
+        xv[k] = K::make(v.x * rs, -v.y * rs);
     }
 }
 
-template <typename K>
-void set_smem_attr(K kernel, size_t bytes) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bytes);
+template <typename Kern>
+void set_smem_attr(Kern kernel, size_t bytes) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
+
+template <typename T, int LT>
+cudaError_t fwd_launch(const FwdArgs<T>& A, bool strided, dim3 grid, size_t smem,
+                       cudaStream_t s) {
+    if (!strided) {
+        set_smem_attr(fft_forward_kernel<T, LT, false>, smem);
+        fft_forward_kernel<T, LT, false><<<grid, NT, smem, s>>>(A);
+    } else {
+        set_smem_attr(fft_forward_kernel<T, LT, true>, smem);
+        fft_forward_kernel<T, LT, true><<<grid, NT, smem, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int LT>
+cudaError_t inv_launch(const InvArgs<T>& A, dim3 grid, size_t smem, cudaStream_t s) {
+    set_smem_attr(fft_inverse_kernel<T, LT>, smem);
+    fft_inverse_kernel<T, LT><<<grid, NT, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+// Dispatch on the half-length: the standard grids get specialised kernels.
+#define SHT_FFT_DISPATCH(L, CALL)          \
+    switch (L) {                           \
+        case 64: return CALL(64);          \
+        case 128: return CALL(128);        \
+        case 256: return CALL(256);        \
+        case 320: return CALL(320);        \
+        case 512: return CALL(512);        \
+        case 640: return CALL(640);        \
+        case 1024: return CALL(1024);      \
+        case 1280: return CALL(1280);      \
+        default: return CALL(0);           \
+    }
 
 template <typename T>
 cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src,
@@ -327,24 +548,20 @@ cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src
     A.grid = static_cast<const T*>(grid);
     A.src = src;
     A.work = static_cast<V*>(work);
-    A.tw = static_cast<const V*>(p->d_tw);
+    A.twp = static_cast<const V*>(p->d_twpass);
     A.twpost = static_cast<const V*>(p->d_twpost);
     A.rev = p->d_rev;
     A.rowscale = sc.rowscale;
     A.mscale0 = sc.mscale0;
     A.mscale1 = sc.mscale1;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
+    A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
-    dim3 grid_dim(p->Jh, (p->F + p->G - 1) / p->G);
-    const size_t smem = p->fft_smem;
-    if (src.elem_stride == 1) {
-        set_smem_attr(fft_forward_kernel<T, false>, smem);
-        fft_forward_kernel<T, false><<<grid_dim, p->fft_threads, smem, s>>>(A);
-    } else {
-        set_smem_attr(fft_forward_kernel<T, true>, smem);
-        fft_forward_kernel<T, true><<<grid_dim, p->fft_threads, smem, s>>>(A);
-    }
-    return cudaGetLastError();
+    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
+    const bool strided = src.elem_stride != 1;
+#define SHT_FWD(LV) fwd_launch<T, LV>(A, strided, g, p->fft_smem, s)
+    SHT_FFT_DISPATCH(p->fft.L, SHT_FWD)
+#undef SHT_FWD
 }
 
 template <typename T>
@@ -354,19 +571,19 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
     InvArgs<T> A;
     A.work = static_cast<const V*>(work);
     A.grid = static_cast<T*>(grid);
-    A.tw = static_cast<const V*>(p->d_tw);
+    A.twp = static_cast<const V*>(p->d_twpass);
     A.twpost = static_cast<const V*>(p->d_twpost);
     A.rev = p->d_rev;
     A.rowscale = sc.rowscale;
     A.mfactor1 = sc.mfactor1;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
+    A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
-    dim3 grid_dim(p->Jh, (p->F + p->G - 1) / p->G);
-    const size_t smem = p->fft_smem;
-    set_smem_attr(fft_inverse_kernel<T>, smem);
-    fft_inverse_kernel<T><<<grid_dim, p->fft_threads, smem, s>>>(A);
-    return cudaGetLastError();
+    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
+#define SHT_INV(LV) inv_launch<T, LV>(A, g, p->fft_smem, s)
+    SHT_FFT_DISPATCH(p->fft.L, SHT_INV)
+#undef SHT_INV
 }
 
 }  // namespace
@@ -374,7 +591,8 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
 size_t fft_smem_bytes(int I, int G, bool fp64) {
     const size_t L = (size_t)I / 2;
     const size_t v = fp64 ? sizeof(double2) : sizeof(float2);
-    return (L + 2 * (size_t)G * L) * v;
+    // padded rows + per-pass twiddle tables (fewer than L entries)
+    return (2 * (size_t)G * fft_row_pitch((int)L, fp64) + L) * v;
 }
 
 cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,

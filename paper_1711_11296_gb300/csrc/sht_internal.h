@@ -28,7 +28,22 @@ struct FftShape {
     int npass = 0;
     int radix[kMaxRadixPasses] = {0};
     int span[kMaxRadixPasses] = {0};   // M_p = L / (r_1 ... r_p)
+    int twoff[kMaxRadixPasses] = {0};  // offset of pass p's twiddle table
+    int twtotal = 0;                   // entries of all per-pass tables
 };
+
+// Shared-memory layout of an FFT row: element pos lives at
+// pos + (pos >> PAD_SHIFT), rows LP = L + (L >> PAD_SHIFT) + 1 apart, so
+// that neither the power-of-two strides of the passes and of the
+// digit-reversed reads nor the row-to-row distance map onto one bank.
+template <typename T> struct PadShift;
+template <> struct PadShift<float> { static constexpr int value = 4; };    // 8-byte complex
+template <> struct PadShift<double> { static constexpr int value = 3; };   // 16-byte complex
+
+inline int fft_row_pitch(int L, bool fp64) {
+    const int s = fp64 ? PadShift<double>::value : PadShift<float>::value;
+    return L + (L >> s) + 1;
+}
 
 // Row-source description for the forward FFT (plain or nested/strided).
 struct RowSource {
@@ -91,6 +106,7 @@ struct sht_plan_s {
     int* d_rev;            // [L] digit-reversed position of frequency k
     void* d_tw;            // [L] e^{-2 pi i e / L}   (double2 or float2)
     void* d_twpost;        // [L] e^{-2 pi i q / I}   (double2 or float2)
+    void* d_twpass;        // per-pass twiddle tables (see FftShape::twoff)
     void* d_work;          // [M][2][Jh][F] complex Fourier workspace
     size_t work_bytes;
 
@@ -98,6 +114,8 @@ struct sht_plan_s {
     int4* d_tiles_fwd; int ntiles_fwd;
     int4* d_tiles_inv; int ntiles_inv;
 
+    int* d_status;             // device status word: kernels OR in failure bits
+                               // (1: tensor-core wait timed out, 2: FFT wait timed out)
     sht::SplitTables* split;   // null for FP64 plans
     sht::Profiler* prof;       // per-launch timing, off by default
 };
@@ -120,6 +138,17 @@ struct ProfScope {
 cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
+cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
+
+// Fill the per-pass twiddle offsets of a factorised FFT shape.
+inline void fft_shape_offsets(FftShape& sh) {
+    int off = 0;
+    for (int q = 0; q < sh.npass; ++q) {
+        sh.twoff[q] = off;
+        off += (sh.radix[q] - 1) * sh.span[q];
+    }
+    sh.twtotal = off;
+}
 
 // FFT launches
 cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,

@@ -98,6 +98,7 @@ bool factor(int L, FftShape& sh) {
         sh.span[q] = span;
     }
     sh.npass = np;
+    fft_shape_offsets(sh);
     return true;
 }
 
@@ -133,7 +134,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     t.ncoef = (size_t)(N + 1) * (N + 2) / 2;
     t.ldp = (t.Jh + 7) / 8 * 8;
     t.fft = shape;
-    const size_t rowbytes = (size_t)shape.L * sizeof(double2);
+    const size_t rowbytes = (size_t)fft_row_pitch(shape.L, true) * sizeof(double2);
     const size_t budget = 110 * 1024;
     long g = (long)((budget / rowbytes > 1 ? budget / rowbytes - 1 : 0) / 2);
     g = g < 1 ? 1 : (g > 16 ? 16 : g);
@@ -160,6 +161,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     const size_t o_rev = off; off += up256(shape.L * sizeof(int));
     const size_t o_tw = off; off += up256(shape.L * sizeof(double2));
     const size_t o_twp = off; off += up256(shape.L * sizeof(double2));
+    const size_t o_tws = off; off += up256((shape.twtotal + 1) * sizeof(double2));
     const size_t o_til = off; off += up256((size_t)t.ntiles_fwd * sizeof(int4));
     const size_t o_wrk = off; off += up256(t.work_bytes);
     if (off > (size_t)SHT_NOALLOC_SCRATCH_BYTES) {
@@ -195,6 +197,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     t.d_rev = (int*)(base + o_rev);
     t.d_tw = base + o_tw;
     t.d_twpost = base + o_twp;
+    t.d_twpass = base + o_tws;
     t.d_tiles_fwd = (int4*)(base + o_til);
     t.d_work = base + o_wrk;
 
@@ -207,6 +210,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     }
     if (e == cudaSuccess) e = launch_pnm_recurrence(&t, s);
     if (e == cudaSuccess) e = launch_twiddles_fp64(&t, s);
+    if (e == cudaSuccess) e = launch_twpass(&t, s);
     if (e == cudaSuccess) {
         rev_kernel<<<(shape.L + th - 1) / th, th, 0, s>>>(shape, t.d_rev);
         e = cudaGetLastError();

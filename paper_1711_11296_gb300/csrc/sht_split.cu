@@ -14,17 +14,19 @@
 // A (the P~ table) is split once at plan time and stored pre-tiled in the
 // canonical no-swizzle K-major layout of the tensor-core shared-memory
 // descriptor: 8 x 8 core matrices of 128 contiguous bytes, core (i8, k8)
-// at ((i8 * TK/8) + k8) * 128 within a K-slab of TK = 32.  A 128-row tile
+// at ((i8 * TK/8) + k8) * 128 within a K-slab of TK = 16.  A 128-row tile
 // of a slab is therefore one contiguous block that one bulk asynchronous
 // copy (TMA engine, cp.async.bulk) moves into shared memory.
-// B (the FP32 Fourier data or spectrum) stays FP32 in HBM; four converter
-// warps load it coalesced, split it into BF16 terms and store it directly
-// in the same K-major core-matrix layout.
+// B (the FP32 Fourier data or spectrum) stays FP32 in HBM.  Its TK rows of
+// a tile arrive by bulk copies too (one per row, 16-byte aligned when the
+// field count is even; otherwise the converters load them directly), and
+// four converter warps split them into BF16 terms, stored in the same
+// K-major core-matrix layout.
 //
-// One CTA computes a 128 x 256 output tile: warps 0-3 convert B and run the
-// epilogue (tcgen05.ld of their 32 TMEM lanes each), warp 4 issues the bulk
-// copies of A, one thread of warp 5 issues tcgen05.mma (M = 128, N = 256,
-// K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
+// One CTA computes a 128 x 256 output tile through a 4-stage pipeline:
+// warps 0-3 convert B and run the epilogue (tcgen05.ld of their 32 TMEM
+// lanes each), warp 4 issues the bulk copies, one thread of warp 5 issues
+// tcgen05.mma (M = 128, N = 256, K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
 // a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
 // waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
@@ -59,21 +61,25 @@ struct SplitTables {
     int4* d_tiles_fwd = nullptr;
     int4* d_tiles_inv = nullptr;
     int ntiles_fwd = 0, ntiles_inv = 0;
-    int* d_status = nullptr;
 };
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 32, UK = 16;
+constexpr int TM = 128, TN = 256, TK = 16, UK = 16;
 constexpr int NTHREADS = 192;
 constexpr int A_TILE_BYTES = TM * TK * 2;   // one term
 constexpr int B_TILE_BYTES = TN * TK * 2;
+constexpr int RAW_BYTES = TK * TN * 4;      // FP32 staging of B: TK rows of TN
+constexpr uint32_t kSBO = (TK / 8) * 128;   // stride between 8-row core groups
 constexpr int TMEM_COLS = 512;        // two 128 x 256 FP32 accumulators
 constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
 
+// Stage layout: T A tiles | FP32 staging of B | T BF16 B tiles.
 template <int T> struct Cfg {
-    static constexpr int NS = T == 3 ? 3 : 4;
-    static constexpr int STAGE_BYTES = T * (A_TILE_BYTES + B_TILE_BYTES);
+    static constexpr int NS = T == 3 ? 4 : 5;
+    static constexpr int RAW_OFF = T * A_TILE_BYTES;
+    static constexpr int BBF_OFF = RAW_OFF + RAW_BYTES;
+    static constexpr int STAGE_BYTES = BBF_OFF + T * B_TILE_BYTES;
     static constexpr int BAR_OFF = NS * STAGE_BYTES;
     static constexpr int SMEM = BAR_OFF + 256;
 };
@@ -86,6 +92,7 @@ struct GemmArgs {
     const float* B;
     float* O;
     int C;                          // valid columns (2F)
+    int raw_bulk;                   // 1: B rows arrive by bulk copy (16-byte aligned)
     int* status;
 };
 
@@ -233,21 +240,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
 
     const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
     if (warp == 4) {
-        // ---- producer of A: one bulk copy per term per stage ----
-        if (lane == 0) {
-            const uint32_t bytes = (uint32_t)h * TK * 2;
-            for (int it = 0; it < nkt; ++it) {
-                const int s = it % NS;
-                const uint32_t ph = (uint32_t)(it / NS) & 1u;
-                if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
-                mbar_expect_tx(full_a(s), bytes * T);
+        // ---- producer: A tiles (lane 0) and the FP32 rows of B (lane k) ----
+        const uint32_t abytes = (uint32_t)h * TK * 2;
+        const int cbase = ct * TN;
+        const int ccopy = min(TN, g.C - cbase);            // valid columns
+        const uint32_t rbytes = (uint32_t)ccopy * 4u;
+        for (int it = 0; it < nkt; ++it) {
+            const int s = it % NS;
+            const uint32_t ph = (uint32_t)(it / NS) & 1u;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            const int k0 = it * TK;
+            const int krows = g.raw_bulk ? max(0, min(TK, pr.K - k0)) : 0;
+            unsigned char* st = smem + s * CF::STAGE_BYTES;
+            if (lane == 0) {
+                mbar_expect_tx(full_a(s), abytes * T + rbytes * (uint32_t)krows);
                 const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
                                           (long long)mt * TM * TK * 2;
-                unsigned char* st = smem + s * CF::STAGE_BYTES;
                 for (int t = 0; t < T; ++t)
                     bulk_g2s(smem_u32(st + t * A_TILE_BYTES),
-                             g.planes + (long long)t * g.plane_bytes + src_off, bytes,
+                             g.planes + (long long)t * g.plane_bytes + src_off, abytes,
                              full_a(s));
+            }
+            __syncwarp();
+            if (lane < krows) {
+                const float* src =
+                    g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase;
+                bulk_g2s(smem_u32(st + CF::RAW_OFF + lane * TN * 4), src, rbytes, full_a(s));
             }
         }
     } else if (warp == 5) {
@@ -261,15 +282,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(smem + s * CF::STAGE_BYTES);
-                const uint32_t bst = st + T * A_TILE_BYTES;
+                const uint32_t bst = st + CF::BBF_OFF;
 #pragma unroll
                 for (int ks = 0; ks < TK / UK; ++ks) {
 #pragma unroll
                     for (int a = 0; a < T; ++a) {
 #pragma unroll
                         for (int b = 0; b < T - a; ++b) {
-                            const uint64_t ad = sdesc(st + a * A_TILE_BYTES + ks * 256, 128, 512);
-                            const uint64_t bd = sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, 512);
+                            const uint64_t ad = sdesc(st + a * A_TILE_BYTES + ks * 256, 128, kSBO);
+                            const uint64_t bd = sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, kSBO);
                             // (0,0) -> leading accumulator; the first of the
                             // others, (0,1), opens the correction accumulator
                             const bool lead = (a == 0 && b == 0);
@@ -286,15 +307,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
         }
     } else {
         // ---- converters: B (FP32, rows k, columns c) -> T BF16 K-major tiles ----
+        // from the staged rows in shared memory (raw_bulk) or straight from
+        // global memory (rows not 16-byte aligned: odd field counts)
         const int tid = threadIdx.x;   // 0..127
         const int cbase = ct * TN;
         for (int it = 0; it < nkt; ++it) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
-            if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
-            unsigned char* bst = smem + s * CF::STAGE_BYTES + T * A_TILE_BYTES;
+            if (g.raw_bulk) {
+                if (!mbar_wait(full_a(s), ph, abort_flag)) break;
+            } else {
+                if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+            }
+            unsigned char* stg = smem + s * CF::STAGE_BYTES;
+            const float* raw = reinterpret_cast<const float*>(stg + CF::RAW_OFF);
+            unsigned char* bst = stg + CF::BBF_OFF;
             const int k0 = it * TK;
-#pragma unroll 2
+#pragma unroll
             for (int v = 0; v < (TN * TK / 8) / 128; ++v) {
                 const int u = tid + 128 * v;
                 const int c = u & (TN - 1);
@@ -303,10 +332,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
                 float x[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int k = k0 + k8 * 8 + e;
-                    x[e] = (k < pr.K && cg < g.C)
-                               ? __ldg(g.B + pr.b_off + (long long)k * pr.b_stride + cg)
-                               : 0.f;
+                    const int kk = k8 * 8 + e;
+                    const bool in = (k0 + kk < pr.K) && (cg < g.C);
+                    if (g.raw_bulk)
+                        x[e] = in ? raw[kk * TN + c] : 0.f;
+                    else
+                        x[e] = in ? __ldg(g.B + pr.b_off + (long long)(k0 + kk) * pr.b_stride + cg)
+                                  : 0.f;
                 }
                 const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
 #pragma unroll
@@ -370,7 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
             }
         }
     }
-    if (*abort_flag && threadIdx.x == 0) atomicOr(g.status, 1);
+    if (*abort_flag && threadIdx.x == 0 && g.status) atomicOr(g.status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -434,7 +466,9 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.B = static_cast<const float*>(B);
     g.O = static_cast<float*>(O);
     g.C = 2 * p->F;
-    g.status = st->d_status;
+    // rows of B are 16-byte aligned when C is a multiple of 4 floats
+    g.raw_bulk = ((g.C & 3) == 0) && (((uintptr_t)B & 15) == 0) ? 1 : 0;
+    g.status = p->d_status;
     const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
     if (ntiles == 0) return cudaSuccess;
     if (st->terms == 3) {
@@ -509,8 +543,7 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
         (e = cudaMalloc(&st->d_probs_fwd, nprob * sizeof(SplitProb))) != cudaSuccess ||
         (e = cudaMalloc(&st->d_probs_inv, nprob * sizeof(SplitProb))) != cudaSuccess ||
         (e = cudaMalloc(&st->d_tiles_fwd, (tf.size() + 1) * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&st->d_tiles_inv, (ti.size() + 1) * sizeof(int4))) != cudaSuccess ||
-        (e = cudaMalloc(&st->d_status, sizeof(int))) != cudaSuccess) {
+        (e = cudaMalloc(&st->d_tiles_inv, (ti.size() + 1) * sizeof(int4))) != cudaSuccess) {
         set_error("split tables: %s", cudaGetErrorString(e));
         return e;
     }
@@ -518,7 +551,6 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
     // planes so K padding and row padding read as zero
     if ((e = cudaMemsetAsync(st->fwd_planes, 0, st->fwd_plane_bytes * st->terms, s)) ||
         (e = cudaMemsetAsync(st->inv_planes, 0, st->inv_plane_bytes * st->terms, s)) ||
-        (e = cudaMemsetAsync(st->d_status, 0, sizeof(int), s)) ||
         (e = cudaMemcpyAsync(st->d_probs_fwd, pf.data(), nprob * sizeof(SplitProb),
                              cudaMemcpyHostToDevice, s)) ||
         (e = cudaMemcpyAsync(st->d_probs_inv, pi.data(), nprob * sizeof(SplitProb),
@@ -542,7 +574,7 @@ void split_tables_destroy(sht_plan_s* p) {
     SplitTables* st = p->split;
     if (!st) return;
     void* ptrs[] = {st->fwd_planes, st->inv_planes, st->d_probs_fwd, st->d_probs_inv,
-                    st->d_tiles_fwd, st->d_tiles_inv, st->d_status};
+                    st->d_tiles_fwd, st->d_tiles_inv};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete st;
@@ -560,11 +592,11 @@ cudaError_t launch_legendre_inv_split(const sht_plan_s* p, const void* spec, voi
 }
 
 int split_status_read_and_clear(const sht_plan_s* p) {
-    if (!p->split || !p->split->d_status) return 0;
+    if (!p->d_status) return 0;
     int v = 0;
-    if (cudaMemcpy(&v, p->split->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return -1;
-    if (v) cudaMemset(p->split->d_status, 0, sizeof(int));
+    if (v) cudaMemset(p->d_status, 0, sizeof(int));
     return v;
 }
 

@@ -104,6 +104,37 @@ __global__ void pnm_kernel(int N, int Jh, int ldp, const double* __restrict__ mu
     }
 }
 
+// Per-pass twiddle tables of the in-place FFT: pass p, entry
+// (k1 - 1) M_p + n1 holds W_L^{n1 k1 L / (r_p M_p)}, gathered from the
+// length-L table so that both are rounded identically.
+template <typename V>
+__global__ void twpass_kernel(const V* __restrict__ tw, FftShape sh, V* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sh.twtotal) return;
+    int p = 0;
+    while (p + 1 < sh.npass && e >= sh.twoff[p + 1]) ++p;
+    const int M = sh.span[p];
+    const int S = sh.radix[p] * M;
+    const int local = e - sh.twoff[p];
+    const int k1 = local / M + 1;
+    const int n1 = local % M;
+    const long long ex = ((long long)n1 * k1 * (sh.L / S)) % sh.L;
+    out[e] = tw[ex];
+}
+
+cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s) {
+    if (p->fft.twtotal == 0) return cudaSuccess;
+    const int threads = 128;
+    const int blocks = (p->fft.twtotal + threads - 1) / threads;
+    if (p->prec == SHT_FP64)
+        twpass_kernel<double2><<<blocks, threads, 0, s>>>((const double2*)p->d_tw, p->fft,
+                                                          (double2*)p->d_twpass);
+    else
+        twpass_kernel<float2><<<blocks, threads, 0, s>>>((const float2*)p->d_tw, p->fft,
+                                                         (float2*)p->d_twpass);
+    return cudaGetLastError();
+}
+
 cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s) {
     const int threads = 128;
     nodes_weights_kernel<<<(p->Jh + threads - 1) / threads, threads, 0, s>>>(
@@ -157,6 +188,8 @@ cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s) {
         twiddle_kernel<float2><<<blocks, threads, 0, s>>>((float2*)p->d_twpost, L, p->I);
     }
     cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    err = launch_twpass(p, s);
     if (err != cudaSuccess) return err;
     // digit-reversed output positions of the in-place mixed-radix FFT
     std::vector<int> rev(L);
