@@ -44,23 +44,8 @@ struct DeviceGuard {
 };
 
 bool factor_fft(int L, FftShape& sh) {
-    sh = FftShape();
-    sh.L = L;
-    int rest = L, np = 0;
-    int radices[kMaxRadixPasses];
-    while (rest % 4 == 0 && np < kMaxRadixPasses) { radices[np++] = 4; rest /= 4; }
-    while (rest % 2 == 0 && np < kMaxRadixPasses) { radices[np++] = 2; rest /= 2; }
-    while (rest % 3 == 0 && np < kMaxRadixPasses) { radices[np++] = 3; rest /= 3; }
-    while (rest % 5 == 0 && np < kMaxRadixPasses) { radices[np++] = 5; rest /= 5; }
-    if (rest != 1) return false;
-    int span = L;
-    for (int q = 0; q < np; ++q) {
-        sh.radix[q] = radices[q];
-        span /= radices[q];
-        sh.span[q] = span;
-    }
-    sh.npass = np;
-    fft_shape_offsets(sh);
+    if (!fft_factorable(L)) return false;
+    sh = fft_factor(L);
     return true;
 }
 
@@ -195,7 +180,7 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
     if (g > 16) g = 16;
     if (g > nfields) g = nfields;
     p->G = (int)g;
-    p->fft_threads = 256;
+    p->fft_threads = 512;
     p->fft_smem = fft_smem_bytes(I, p->G, fp64);
     if (p->fft_smem > 227 * 1024) {
         delete p;

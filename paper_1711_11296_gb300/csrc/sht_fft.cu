@@ -3,7 +3,7 @@
 // the per-m Legendre contraction wants.
 //
 // A row of I real samples x_i is read as L = I/2 complex values
-// z_k = x_{2k} + i x_{2k+1}; an in-place mixed-radix (2/3/4/5) decimation-in-
+// z_k = x_{2k} + i x_{2k+1}; an in-place mixed-radix (2/3/4/5/8) decimation-in-
 // frequency FFT of length L runs in shared memory and leaves Z in
 // digit-reversed order (rev(k) = position of frequency k).  The real
 // spectrum follows from
@@ -35,7 +35,7 @@
 namespace sht {
 namespace {
 
-constexpr int NT = 256;   // threads per FFT CTA
+constexpr int NT = 512;   // threads per FFT CTA (two CTAs per SM)
 
 template <typename T> struct C2 {
     using V = typename Vec2<T>::type;
@@ -53,38 +53,9 @@ template <typename T> struct C2 {
     static __device__ __forceinline__ V mul_pi(V a) { return make(-a.y, a.x); }
 };
 
-// Compile-time factorisation; the same rule as the plan's (4s, 2s, 3s, 5s).
-struct Fac {
-    int L = 0, npass = 0, twtotal = 0;
-    int radix[kMaxRadixPasses] = {0};
-    int span[kMaxRadixPasses] = {0};
-    int twoff[kMaxRadixPasses] = {0};
-};
-
-constexpr Fac make_fac(int L) {
-    Fac f{};
-    f.L = L;
-    int rest = L, np = 0;
-    const int cand[4] = {4, 2, 3, 5};
-    for (int c = 0; c < 4; ++c)
-        while (rest % cand[c] == 0 && np < kMaxRadixPasses) {
-            f.radix[np++] = cand[c];
-            rest /= cand[c];
-        }
-    int span = L, off = 0;
-    for (int q = 0; q < np; ++q) {
-        span /= f.radix[q];
-        f.span[q] = span;
-        f.twoff[q] = off;
-        off += (f.radix[q] - 1) * span;
-    }
-    f.npass = np;
-    f.twtotal = off;
-    return f;
-}
-
+// The plan's factorisation as a compile-time constant.
 template <int L> struct FacOf {
-    static constexpr Fac v = make_fac(L);
+    static constexpr FftShape v = fft_factor(L);
 };
 
 template <typename T>
@@ -130,6 +101,31 @@ template <typename T> struct Dft<T, 4> {
         a[2] = K::sub(s02, s13);
         a[1] = K::add(d02, d13);
         a[3] = K::sub(d02, d13);
+    }
+};
+
+template <typename T> struct Dft<T, 8> {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ void run(V* a) {
+        using K = C2<T>;
+        const T r = (T)0.70710678118654752440;   // 1/sqrt(2)
+        // even and odd halves by radix 4, then y_k = E_k + W8^k O_k,
+        // y_{k+4} = E_k - W8^k O_k with W8 = e^{-2 pi i/8}
+        V e[4] = {a[0], a[2], a[4], a[6]};
+        V o[4] = {a[1], a[3], a[5], a[7]};
+        Dft<T, 4>::run(e);
+        Dft<T, 4>::run(o);
+        const V o1 = K::make(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));   // W8^1 o1
+        const V o2 = K::mul_mi(o[2]);                                          // W8^2 o2
+        const V o3 = K::make(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));   // W8^3 o3
+        a[0] = K::add(e[0], o[0]);
+        a[4] = K::sub(e[0], o[0]);
+        a[1] = K::add(e[1], o1);
+        a[5] = K::sub(e[1], o1);
+        a[2] = K::add(e[2], o2);
+        a[6] = K::sub(e[2], o2);
+        a[3] = K::add(e[3], o3);
+        a[7] = K::sub(e[3], o3);
     }
 };
 
@@ -201,7 +197,9 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
             const int n1 = b - blk * M;
             auto* z = rows + (size_t)row * LP;
             const int base = blk * S + n1;
-            if (r == 4)
+            if (r == 8)
+                bfly<T, 8>(z, base, M, tw, n1);
+            else if (r == 4)
                 bfly<T, 4>(z, base, M, tw, n1);
             else if (r == 2)
                 bfly<T, 2>(z, base, M, tw, n1);
@@ -218,7 +216,7 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
 template <typename T, int L, int P>
 __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int nrows, int LP,
                                              const typename Vec2<T>::type* twp) {
-    constexpr Fac F = FacOf<L>::v;
+    constexpr FftShape F = FacOf<L>::v;
     if constexpr (P < F.npass) {
         constexpr int R = F.radix[P];
         constexpr int M = F.span[P];
@@ -241,7 +239,7 @@ __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int n
 // Digit-reversed position of frequency k.
 template <int L>
 __device__ __forceinline__ int rev_fixed(int k) {
-    constexpr Fac F = FacOf<L>::v;
+    constexpr FftShape F = FacOf<L>::v;
     int pos = 0;
 #pragma unroll
     for (int q = 0; q < F.npass; ++q) {
@@ -325,7 +323,7 @@ struct Walk2 {
 };
 
 template <typename T, int LT, bool STRIDED>
-__global__ void __launch_bounds__(NT) fft_forward_kernel(FwdArgs<T> A) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_forward_kernel(FwdArgs<T> A) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -409,7 +407,7 @@ __global__ void __launch_bounds__(NT) fft_forward_kernel(FwdArgs<T> A) {
 }
 
 template <typename T, int LT>
-__global__ void __launch_bounds__(NT) fft_inverse_kernel(InvArgs<T> A) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_inverse_kernel(InvArgs<T> A) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -140,14 +140,35 @@ cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
 cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
 
-// Fill the per-pass twiddle offsets of a factorised FFT shape.
-inline void fft_shape_offsets(FftShape& sh) {
-    int off = 0;
-    for (int q = 0; q < sh.npass; ++q) {
+// Mixed-radix factorisation of the half-length FFT, shared by the plans,
+// the allocation-free entry point and the compile-time kernels: radices 8
+// first (fewest shared-memory passes), then 4, 2, 3, 5; spans and per-pass
+// twiddle offsets follow.  npass = 0 and L != 1 means "not factorable".
+__host__ __device__ constexpr FftShape fft_factor(int L) {
+    FftShape sh{};
+    sh.L = L;
+    int rest = L, np = 0;
+    const int cand[5] = {8, 4, 2, 3, 5};
+    for (int c = 0; c < 5; ++c)
+        while (rest % cand[c] == 0 && np < kMaxRadixPasses) {
+            sh.radix[np++] = cand[c];
+            rest /= cand[c];
+        }
+    if (rest != 1) return FftShape{};
+    int span = L, off = 0;
+    for (int q = 0; q < np; ++q) {
+        span /= sh.radix[q];
+        sh.span[q] = span;
         sh.twoff[q] = off;
-        off += (sh.radix[q] - 1) * sh.span[q];
+        off += (sh.radix[q] - 1) * span;
     }
+    sh.npass = np;
     sh.twtotal = off;
+    return sh;
+}
+
+__host__ __device__ constexpr bool fft_factorable(int L) {
+    return L == 1 || fft_factor(L).npass > 0;
 }
 
 // FFT launches

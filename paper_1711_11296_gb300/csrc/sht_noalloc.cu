@@ -82,23 +82,8 @@ __global__ void rev_kernel(FftShape sh, int* rev) {
 }
 
 bool factor(int L, FftShape& sh) {
-    sh = FftShape();
-    sh.L = L;
-    int rest = L, np = 0;
-    const int cand[4] = {4, 2, 3, 5};
-    for (int c = 0; c < 4; ++c)
-        while (rest % cand[c] == 0 && np < kMaxRadixPasses) {
-            sh.radix[np++] = cand[c];
-            rest /= cand[c];
-        }
-    if (rest != 1) return false;
-    int span = L;
-    for (int q = 0; q < np; ++q) {
-        span /= sh.radix[q];
-        sh.span[q] = span;
-    }
-    sh.npass = np;
-    fft_shape_offsets(sh);
+    if (!fft_factorable(L)) return false;
+    sh = fft_factor(L);
     return true;
 }
 
@@ -139,7 +124,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     long g = (long)((budget / rowbytes > 1 ? budget / rowbytes - 1 : 0) / 2);
     g = g < 1 ? 1 : (g > 16 ? 16 : g);
     t.G = (int)(g > nfields ? nfields : g);
-    t.fft_threads = 256;
+    t.fft_threads = 512;
     t.fft_smem = fft_smem_bytes(I, t.G, true);
     if (t.fft_smem > 227 * 1024) {
         set_error("I = %d too large for the shared-memory FFT", I);

@@ -23,10 +23,13 @@
 // four converter warps split them into BF16 terms, stored in the same
 // K-major core-matrix layout.
 //
-// One CTA computes a 128 x 256 output tile through a 4-stage pipeline:
-// warps 0-3 convert B and run the epilogue (tcgen05.ld of their 32 TMEM
-// lanes each), warp 4 issues the bulk copies, one thread of warp 5 issues
-// tcgen05.mma (M = 128, N = 256, K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
+// One CTA computes a 128 x 128 output tile through a 3-stage pipeline
+// (two CTAs share an SM, so one's prologue and epilogue overlap the
+// other's main loop):
+// warps 0-7 convert B and run the epilogue (tcgen05.ld of the 32 TMEM lanes
+// a warp may access, for half of the columns each), warp 8 issues the bulk
+// copies, one thread of warp 9 issues tcgen05.mma (M = 128, N = 128,
+// K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
 // a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
 // waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
@@ -65,18 +68,20 @@ struct SplitTables {
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 16, UK = 16;
-constexpr int NTHREADS = 192;
+constexpr int TM = 128, TN = 128, TK = 16, UK = 16;
+constexpr int NCONV = 256;                 // converter / epilogue threads (8 warps)
+constexpr int NTHREADS = NCONV + 64;       // + bulk-copy warp + MMA warp
+constexpr int WARP_PRODUCER = NCONV / 32, WARP_MMA = NCONV / 32 + 1;
 constexpr int A_TILE_BYTES = TM * TK * 2;   // one term
 constexpr int B_TILE_BYTES = TN * TK * 2;
 constexpr int RAW_BYTES = TK * TN * 4;      // FP32 staging of B: TK rows of TN
 constexpr uint32_t kSBO = (TK / 8) * 128;   // stride between 8-row core groups
-constexpr int TMEM_COLS = 512;        // two 128 x 256 FP32 accumulators
+constexpr int TMEM_COLS = 2 * TN;     // two 128 x TN FP32 accumulators
 constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
 
 // Stage layout: T A tiles | FP32 staging of B | T BF16 B tiles.
 template <int T> struct Cfg {
-    static constexpr int NS = T == 3 ? 4 : 5;
+    static constexpr int NS = T == 3 ? 3 : 4;   // <= 113 KB: two CTAs per SM
     static constexpr int RAW_OFF = T * A_TILE_BYTES;
     static constexpr int BBF_OFF = RAW_OFF + RAW_BYTES;
     static constexpr int STAGE_BYTES = BBF_OFF + T * B_TILE_BYTES;
@@ -195,7 +200,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 template <int T>
-__global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(GemmArgs g) {
     using CF = Cfg<T>;
     constexpr int NS = CF::NS;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full_a(s), 1);
-            mbar_init(full_b(s), 128);
+            mbar_init(full_b(s), NCONV);
             mbar_init(empty(s), 1);
         }
         mbar_init(done, 1);
@@ -239,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
     const uint32_t tmem = *tmem_slot;
 
     const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
-    if (warp == 4) {
+    if (warp == WARP_PRODUCER) {
         // ---- producer: A tiles (lane 0) and the FP32 rows of B (lane k) ----
         const uint32_t abytes = (uint32_t)h * TK * 2;
         const int cbase = ct * TN;
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
                 bulk_g2s(smem_u32(st + CF::RAW_OFF + lane * TN * 4), src, rbytes, full_a(s));
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == WARP_MMA) {
         // ---- MMA issuer ----
         if (lane == 0) {
             bool ok = true;
@@ -309,7 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
         // ---- converters: B (FP32, rows k, columns c) -> T BF16 K-major tiles ----
         // from the staged rows in shared memory (raw_bulk) or straight from
         // global memory (rows not 16-byte aligned: odd field counts)
-        const int tid = threadIdx.x;   // 0..127
+        const int tid = threadIdx.x;   // 0..NCONV-1
         const int cbase = ct * TN;
         for (int it = 0; it < nkt; ++it) {
             const int s = it % NS;
@@ -324,10 +329,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
             unsigned char* bst = stg + CF::BBF_OFF;
             const int k0 = it * TK;
 #pragma unroll
-            for (int v = 0; v < (TN * TK / 8) / 128; ++v) {
-                const int u = tid + 128 * v;
-                const int c = u & (TN - 1);
-                const int k8 = u >> 8;
+            for (int v = 0; v < (TN * TK / 8) / NCONV; ++v) {
+                const int u = tid + NCONV * v;
+                const int c = u % TN;
+                const int k8 = u / TN;
                 const int cg = cbase + c;
                 float x[8];
 #pragma unroll
@@ -361,21 +366,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(full_b(s));
         }
-        // ---- epilogue: TMEM lanes 32*warp .. +31 = tile rows ----
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the tile
+        // rows it may access) for column half w / 4 ----
         const bool have = nkt > 0;
         bool ok = true;
         if (have) ok = mbar_wait(done, 0, abort_flag);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int row = TM * mt + 32 * warp + lane;
+        const int lq = warp & 3, half = warp >> 2;
+        const int row = TM * mt + 32 * lq + lane;
         const bool row_ok = row < pr.Mrows && ok && !*abort_flag;
         float* orow = g.O + pr.o_off + (long long)row * pr.o_stride;
         const bool vec = ((pr.o_stride & 3) == 0) && ((pr.o_off & 3) == 0) &&
                          ((g.C & 3) == 0);
-        for (int ch = 0; ch < TN / 16; ++ch) {
+        constexpr int NCH = TN / 16 / (NCONV / 128);
+        for (int cc = 0; cc < NCH; ++cc) {
+            const int ch = half * NCH + cc;
             uint32_t r[16];
             if (have && ok) {
                 uint32_t r2[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(ch * 16);
+                const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
                 tmem_ld16(ta, r);
                 tmem_ld16(ta + TN, r2);
 #pragma unroll
@@ -398,7 +407,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) split_gemm_kernel(GemmArgs g) {
                     *reinterpret_cast<float4*>(orow + c0 + 4 * i) = f;
                 }
             } else {
-                for (int i = 0; i < 16 && c0 + i < g.C; ++i) orow[c0 + i] = __uint_as_float(r[i]);
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < g.C) orow[c0 + i] = __uint_as_float(r[i]);
             }
         }
     }
