@@ -148,6 +148,28 @@ int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
 int sht_forward_noalloc(int N, int J, int I, int nfields, const double* grid,
                         double* spec, void* stream);
 
+/* Groups: several plans (for example uneven truncations of an ensemble, or
+ * the levels of a multigrid ladder) transformed by one launch per kernel
+ * stage, so that a batch is four launches per transform pair and fits in
+ * one CUDA graph.  The paper has no counterpart; the per-plan results are
+ * those of sht_forward / sht_inverse on each plan.
+ *   plans: 1..8 live plans of one precision on one device, each at most
+ *   once (their workspaces are used).  The group refers to the plans; they
+ *   must outlive it.  Returns SHT_ERR_ARG or SHT_ERR_HANDLE otherwise. */
+typedef struct sht_group_s* sht_group_t;
+int sht_group_create(const sht_plan_t* plans, int nplans, sht_group_t* out);
+int sht_group_destroy(sht_group_t group);
+
+/* Analysis of every plan's grid: grids[q] and specs[q] are the device
+ * buffers of plan q (host arrays of nplans pointers), layouts as for
+ * sht_forward.  Calls of a group, and of its plans, must not overlap. */
+int sht_group_forward(sht_group_t group, const void* const* grids, void* const* specs,
+                      void* stream);
+
+/* Synthesis of every plan's spectrum, as sht_inverse per plan. */
+int sht_group_inverse(sht_group_t group, const void* const* specs, void* const* grids,
+                      void* stream);
+
 /* Synchronise the plan's device and report device-side failures of the
  * plan's kernels since the last call: SHT_ERR_TIMEOUT if a kernel gave
  * up on one of its bounded waits (a tensor-core pipeline stage or an

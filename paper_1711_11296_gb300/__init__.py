@@ -7,7 +7,7 @@ input generators in ``workloads`` stay usable without the built library.
 
 
 def __getattr__(name):
-    if name in ("Plan", "Analysis", "Synthesis", "analysis", "synthesis",
+    if name in ("Plan", "Group", "Analysis", "Synthesis", "analysis", "synthesis",
                 "SHTError"):
         from . import sht
         return getattr(sht, name)

@@ -15,7 +15,8 @@ EXPORTED = [
     "sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_forward",
     "sht_inverse", "sht_adjoint", "sht_restrict_nested", "sht_plan_copy_tables",
     "sht_profile_enable", "sht_profile_read", "sht_last_error", "sht_version",
-    "sht_forward_noalloc", "sht_plan_status",
+    "sht_forward_noalloc", "sht_plan_status", "sht_group_create",
+    "sht_group_destroy", "sht_group_forward", "sht_group_inverse",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -58,6 +59,11 @@ def _load():
     lib.sht_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     lib.sht_forward_noalloc.argtypes = [i, i, i, i, vp, vp, vp]
     lib.sht_plan_status.argtypes = [vp]
+    vpp = ctypes.POINTER(vp)
+    lib.sht_group_create.argtypes = [vpp, i, ctypes.POINTER(vp)]
+    lib.sht_group_destroy.argtypes = [vp]
+    lib.sht_group_forward.argtypes = [vp, vpp, vpp, vp]
+    lib.sht_group_inverse.argtypes = [vp, vpp, vpp, vp]
     lib.sht_last_error.restype = ctypes.c_char_p
     lib.sht_version.restype = ctypes.c_char_p
     for name in EXPORTED:

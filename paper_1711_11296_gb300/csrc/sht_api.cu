@@ -5,6 +5,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <map>
 #include <mutex>
 #include <new>
 #include <set>
@@ -94,6 +95,21 @@ void set_error(const char* fmt, ...) {
 bool plan_is_live(const sht_plan_s* p) {
     std::lock_guard<std::mutex> lk(g_live_mu);
     return g_live.count(p) != 0 && p->magic == kPlanMagic;
+}
+
+cudaError_t ensure_smem(const void* kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& have = done[{dev, kernel}];
+    if (bytes <= have) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
 }
 
 cudaEvent_t Profiler::get() {

@@ -322,17 +322,17 @@ struct Walk2 {
     }
 };
 
+extern __shared__ __align__(16) unsigned char fft_smem_raw[];
+
 template <typename T, int LT, bool STRIDED>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_forward_kernel(FwdArgs<T> A) {
+__device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = LT > 0 ? LT : A.L;
     const int LP = A.LP;
-    V* rows = reinterpret_cast<V*>(smem_raw);
+    V* rows = reinterpret_cast<V*>(fft_smem_raw);
     V* tws = rows + (size_t)2 * A.G * LP;
-    const int jh = blockIdx.y;
-    const int f0 = blockIdx.x * A.G;
+    const int f0 = fg * A.G;
     const int nf = min(A.G, A.F - f0);
     const bool equator = (jh == A.Jh - 1);
     const int nrows = equator ? nf : 2 * nf;
@@ -406,17 +406,21 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_forward_kernel
     }
 }
 
+template <typename T, int LT, bool STRIDED>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_forward_kernel(const __grid_constant__ FwdArgs<T> A) {
+    fwd_body<T, LT, STRIDED>(A, blockIdx.x, blockIdx.y);
+}
+
 template <typename T, int LT>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_inverse_kernel(InvArgs<T> A) {
+__device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     using V = typename Vec2<T>::type;
     using K = C2<T>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int L = LT > 0 ? LT : A.L;
     const int LP = A.LP;
-    V* rows = reinterpret_cast<V*>(smem_raw);
+    V* rows = reinterpret_cast<V*>(fft_smem_raw);
     V* tws = rows + (size_t)2 * A.G * LP;
-    const int jh = blockIdx.y;
-    const int f0 = blockIdx.x * A.G;
+    const int f0 = fg * A.G;
     const int nf = min(A.G, A.F - f0);
     const bool equator = (jh == A.Jh - 1);
     const int nrows = equator ? nf : 2 * nf;
@@ -499,19 +503,56 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) fft_inverse_kernel
     }
 }
 
-template <typename Kern>
-void set_smem_attr(Kern kernel, size_t bytes) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+template <typename T, int LT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_inverse_kernel(const __grid_constant__ InvArgs<T> A) {
+    inv_body<T, LT>(A, blockIdx.x, blockIdx.y);
+}
+
+// ---- grouped launches: several plans' rows in one grid ----------------
+template <typename T> struct FwdGroup {
+    int n;
+    int cta_start[kMaxGroup + 1];   // first CTA of each plan
+    int nfg[kMaxGroup];             // field groups per latitude of each plan
+    FwdArgs<T> a[kMaxGroup];
+};
+
+template <typename T> struct InvGroup {
+    int n;
+    int cta_start[kMaxGroup + 1];
+    int nfg[kMaxGroup];
+    InvArgs<T> a[kMaxGroup];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_forward_group_kernel(const __grid_constant__ FwdGroup<T> G) {
+    const int b = blockIdx.x;
+    int p = 0;
+    while (p + 1 < G.n && b >= G.cta_start[p + 1]) ++p;
+    const int local = b - G.cta_start[p];
+    fwd_body<T, 0, false>(G.a[p], local % G.nfg[p], local / G.nfg[p]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_inverse_group_kernel(const __grid_constant__ InvGroup<T> G) {
+    const int b = blockIdx.x;
+    int p = 0;
+    while (p + 1 < G.n && b >= G.cta_start[p + 1]) ++p;
+    const int local = b - G.cta_start[p];
+    inv_body<T, 0>(G.a[p], local % G.nfg[p], local / G.nfg[p]);
 }
 
 template <typename T, int LT>
 cudaError_t fwd_launch(const FwdArgs<T>& A, bool strided, dim3 grid, size_t smem,
                        cudaStream_t s) {
+    cudaError_t e;
     if (!strided) {
-        set_smem_attr(fft_forward_kernel<T, LT, false>, smem);
+        if ((e = ensure_smem((const void*)fft_forward_kernel<T, LT, false>, smem))) return e;
         fft_forward_kernel<T, LT, false><<<grid, NT, smem, s>>>(A);
     } else {
-        set_smem_attr(fft_forward_kernel<T, LT, true>, smem);
+        if ((e = ensure_smem((const void*)fft_forward_kernel<T, LT, true>, smem))) return e;
         fft_forward_kernel<T, LT, true><<<grid, NT, smem, s>>>(A);
     }
     return cudaGetLastError();
@@ -519,7 +560,8 @@ cudaError_t fwd_launch(const FwdArgs<T>& A, bool strided, dim3 grid, size_t smem
 
 template <typename T, int LT>
 cudaError_t inv_launch(const InvArgs<T>& A, dim3 grid, size_t smem, cudaStream_t s) {
-    set_smem_attr(fft_inverse_kernel<T, LT>, smem);
+    cudaError_t e = ensure_smem((const void*)fft_inverse_kernel<T, LT>, smem);
+    if (e) return e;
     fft_inverse_kernel<T, LT><<<grid, NT, smem, s>>>(A);
     return cudaGetLastError();
 }
@@ -539,8 +581,8 @@ cudaError_t inv_launch(const InvArgs<T>& A, dim3 grid, size_t smem, cudaStream_t
     }
 
 template <typename T>
-cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src,
-                     const FwdScale& sc, void* work, cudaStream_t s) {
+FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource& src,
+                         const FwdScale& sc, void* work) {
     using V = typename Vec2<T>::type;
     FwdArgs<T> A;
     A.grid = static_cast<const T*>(grid);
@@ -555,6 +597,13 @@ cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
+    return A;
+}
+
+template <typename T>
+cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src,
+                     const FwdScale& sc, void* work, cudaStream_t s) {
+    const FwdArgs<T> A = make_fwd_args<T>(p, grid, src, sc, work);
     const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
     const bool strided = src.elem_stride != 1;
 #define SHT_FWD(LV) fwd_launch<T, LV>(A, strided, g, p->fft_smem, s)
@@ -563,8 +612,8 @@ cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src
 }
 
 template <typename T>
-cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
-                     void* grid, cudaStream_t s) {
+InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& sc,
+                         void* grid) {
     using V = typename Vec2<T>::type;
     InvArgs<T> A;
     A.work = static_cast<const V*>(work);
@@ -578,13 +627,79 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
+    return A;
+}
+
+template <typename T>
+cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
+                     void* grid, cudaStream_t s) {
+    const InvArgs<T> A = make_inv_args<T>(p, work, sc, grid);
     const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
 #define SHT_INV(LV) inv_launch<T, LV>(A, g, p->fft_smem, s)
     SHT_FFT_DISPATCH(p->fft.L, SHT_INV)
 #undef SHT_INV
 }
 
+template <typename T>
+cudaError_t fwd_group_impl(sht_plan_s* const* plans, int n, const void* const* grids,
+                           cudaStream_t s) {
+    FwdGroup<T> G;
+    G.n = n;
+    G.cta_start[0] = 0;
+    size_t smem = 0;
+    for (int q = 0; q < n; ++q) {
+        const sht_plan_s* p = plans[q];
+        RowSource src;
+        src.field_stride = (long long)p->J * p->I;
+        src.row_stride = p->I;
+        src.row_offset = 0;
+        src.elem_stride = 1;
+        const FwdScale sc{p->d_w_over_I, 1.0, 1.0};
+        G.a[q] = make_fwd_args<T>(p, grids[q], src, sc, p->d_work);
+        G.nfg[q] = (p->F + p->G - 1) / p->G;
+        G.cta_start[q + 1] = G.cta_start[q] + G.nfg[q] * p->Jh;
+        if (p->fft_smem > smem) smem = p->fft_smem;
+    }
+    cudaError_t e = ensure_smem((const void*)fft_forward_group_kernel<T>, smem);
+    if (e) return e;
+    fft_forward_group_kernel<T><<<G.cta_start[n], NT, smem, s>>>(G);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t inv_group_impl(sht_plan_s* const* plans, int n, void* const* grids,
+                           cudaStream_t s) {
+    InvGroup<T> G;
+    G.n = n;
+    G.cta_start[0] = 0;
+    size_t smem = 0;
+    for (int q = 0; q < n; ++q) {
+        const sht_plan_s* p = plans[q];
+        const InvScale sc{nullptr, 1.0};
+        G.a[q] = make_inv_args<T>(p, p->d_work, sc, grids[q]);
+        G.nfg[q] = (p->F + p->G - 1) / p->G;
+        G.cta_start[q + 1] = G.cta_start[q] + G.nfg[q] * p->Jh;
+        if (p->fft_smem > smem) smem = p->fft_smem;
+    }
+    cudaError_t e = ensure_smem((const void*)fft_inverse_group_kernel<T>, smem);
+    if (e) return e;
+    fft_inverse_group_kernel<T><<<G.cta_start[n], NT, smem, s>>>(G);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_fft_forward_group(sht_plan_s* const* plans, int n,
+                                     const void* const* grids, cudaStream_t s) {
+    if (plans[0]->prec == SHT_FP64) return fwd_group_impl<double>(plans, n, grids, s);
+    return fwd_group_impl<float>(plans, n, grids, s);
+}
+
+cudaError_t launch_fft_inverse_group(sht_plan_s* const* plans, int n,
+                                     void* const* grids, cudaStream_t s) {
+    if (plans[0]->prec == SHT_FP64) return inv_group_impl<double>(plans, n, grids, s);
+    return inv_group_impl<float>(plans, n, grids, s);
+}
 
 size_t fft_smem_bytes(int I, int G, bool fp64) {
     const size_t L = (size_t)I / 2;

@@ -14,6 +14,12 @@ namespace sht {
 constexpr uint64_t kPlanMagic = 0x53485450'4C414E31ull;   // "SHTPLAN1"
 constexpr int kMaxRadixPasses = 16;
 constexpr int kMaxI = 8192;
+constexpr int kMaxGroup = 8;    // plans per grouped launch
+
+// Raise a kernel's dynamic shared-memory limit on the current device the
+// first time a launch needs more than 48 KB (later launches, e.g. under
+// stream capture, make no host API call).  Returns the CUDA status.
+cudaError_t ensure_smem(const void* kernel, size_t bytes);
 
 // Thread-local error message set by the C entry points.
 void set_error(const char* fmt, ...);
@@ -177,6 +183,11 @@ cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,
                                void* work, cudaStream_t s);
 cudaError_t launch_fft_inverse(const sht_plan_s* p, const void* work,
                                const InvScale& sc, void* grid, cudaStream_t s);
+// One launch over n plans (same precision): plain analysis / synthesis FFTs.
+cudaError_t launch_fft_forward_group(sht_plan_s* const* plans, int n,
+                                     const void* const* grids, cudaStream_t s);
+cudaError_t launch_fft_inverse_group(sht_plan_s* const* plans, int n,
+                                     void* const* grids, cudaStream_t s);
 size_t fft_smem_bytes(int I, int G, bool fp64);
 
 // FP64 Legendre launches

@@ -31,14 +31,12 @@ __device__ __forceinline__ size_t dcoef_offset(int N, int m) {
     return (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
 }
 
-__global__ void __launch_bounds__(NT) legendre_fwd_fp64_kernel(
+__device__ __forceinline__ void legendre_fwd_body(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ work,
-    double* __restrict__ spec, const int4* __restrict__ tiles, int N, int Jh,
-    int C) {
+    double* __restrict__ spec, int4 t, int N, int Jh, int C) {
     __shared__ double Ps[BK][BM + 1];
     __shared__ double Bs[BK][BN];
-    const int4 t = tiles[blockIdx.x];
-    const int m = t.x, q = t.y, r0 = t.z, c0 = t.w;
+    const int m = t.x, q = t.y & 1, r0 = t.z, c0 = t.w;
     const int R = parity_rows(N, m, q);
     const size_t row0 = dcoef_offset(N, m) + q;     // packed row of n = m + q
     const double* B = work + ((size_t)(2 * m + q) * Jh) * C;
@@ -85,14 +83,12 @@ __global__ void __launch_bounds__(NT) legendre_fwd_fp64_kernel(
     }
 }
 
-__global__ void __launch_bounds__(NT) legendre_inv_fp64_kernel(
+__device__ __forceinline__ void legendre_inv_body(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ spec,
-    double* __restrict__ work, const int4* __restrict__ tiles, int N, int Jh,
-    int C) {
+    double* __restrict__ work, int4 t, int N, int Jh, int C) {
     __shared__ double Ps[BK][BM];
     __shared__ double Bs[BK][BN];
-    const int4 t = tiles[blockIdx.x];
-    const int m = t.x, q = t.y, j0 = t.z, c0 = t.w;
+    const int m = t.x, q = t.y & 1, j0 = t.z, c0 = t.w;
     const int R = parity_rows(N, m, q);
     const size_t row0 = dcoef_offset(N, m) + q;
     const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
@@ -138,7 +134,64 @@ __global__ void __launch_bounds__(NT) legendre_inv_fp64_kernel(
     }
 }
 
+__global__ void __launch_bounds__(NT) legendre_fwd_fp64_kernel(
+    const double* __restrict__ pnm, int ldp, const double* __restrict__ work,
+    double* __restrict__ spec, const int4* __restrict__ tiles, int N, int Jh, int C) {
+    legendre_fwd_body(pnm, ldp, work, spec, tiles[blockIdx.x], N, Jh, C);
+}
+
+__global__ void __launch_bounds__(NT) legendre_inv_fp64_kernel(
+    const double* __restrict__ pnm, int ldp, const double* __restrict__ spec,
+    double* __restrict__ work, const int4* __restrict__ tiles, int N, int Jh, int C) {
+    legendre_inv_body(pnm, ldp, spec, work, tiles[blockIdx.x], N, Jh, C);
+}
+
+// Grouped launches: tile.y = parity + 2 * (plan index in the group).
+struct LegGroup {
+    int n;
+    const double* pnm[kMaxGroup];
+    const double* in[kMaxGroup];
+    double* out[kMaxGroup];
+    int ldp[kMaxGroup], N[kMaxGroup], Jh[kMaxGroup], C[kMaxGroup];
+};
+
+__global__ void __launch_bounds__(NT) legendre_fwd_fp64_group_kernel(
+    const __grid_constant__ LegGroup G, const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const int p = t.y >> 1;
+    legendre_fwd_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p]);
+}
+
+__global__ void __launch_bounds__(NT) legendre_inv_fp64_group_kernel(
+    const __grid_constant__ LegGroup G, const int4* __restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const int p = t.y >> 1;
+    legendre_inv_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p]);
+}
+
 }  // namespace
+
+cudaError_t launch_legendre_fp64_group(sht_plan_s* const* plans, int n, bool inverse,
+                                       const void* const* in, void* const* out,
+                                       const int4* tiles, int ntiles, cudaStream_t s) {
+    LegGroup G;
+    G.n = n;
+    for (int q = 0; q < n; ++q) {
+        G.pnm[q] = plans[q]->d_pnm;
+        G.ldp[q] = plans[q]->ldp;
+        G.N[q] = plans[q]->N;
+        G.Jh[q] = plans[q]->Jh;
+        G.C[q] = 2 * plans[q]->F;
+        G.in[q] = static_cast<const double*>(in[q]);
+        G.out[q] = static_cast<double*>(out[q]);
+    }
+    if (ntiles == 0) return cudaSuccess;
+    if (inverse)
+        legendre_inv_fp64_group_kernel<<<ntiles, NT, 0, s>>>(G, tiles);
+    else
+        legendre_fwd_fp64_group_kernel<<<ntiles, NT, 0, s>>>(G, tiles);
+    return cudaGetLastError();
+}
 
 // Tile lists (host): forward tiles cover the parity rows of each (m, q);
 // inverse tiles cover the Jh northern rows of each (m, q), including the

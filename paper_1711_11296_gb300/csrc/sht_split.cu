@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "sht_internal.h"
@@ -199,11 +200,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+extern __shared__ __align__(1024) unsigned char split_smem[];
+
 template <int T>
-__global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(GemmArgs g) {
+__device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 tile) {
     using CF = Cfg<T>;
     constexpr int NS = CF::NS;
-    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
     // bars: full_a[NS], full_b[NS], empty[NS], done
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1));
@@ -211,7 +214,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(GemmArgs g) {
         reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1) + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int4 tile = g.tiles[blockIdx.x];
     const SplitProb pr = g.probs[tile.x];
     const int mt = tile.y, ct = tile.z;
     const int nkt = pr.nkt;
@@ -431,6 +433,25 @@ __global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(GemmArgs g) {
     }
 }
 
+template <int T>
+__global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(const __grid_constant__ GemmArgs g) {
+    split_gemm_body<T>(g, g.tiles[blockIdx.x]);
+}
+
+// Grouped launch: tile.w is the plan's index in the group.
+struct GemmGroup {
+    int n;
+    GemmArgs a[kMaxGroup];
+    const int4* tiles;
+};
+
+template <int T>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    split_gemm_group_kernel(const __grid_constant__ GemmGroup G) {
+    const int4 t = G.tiles[blockIdx.x];
+    split_gemm_body<T>(G.a[t.w], t);
+}
+
 // Split the FP64 P~ table into T BF16 planes, pre-tiled (see top of file).
 // One block per (m, parity) problem.  fwd: A rows are the parity rows n_r,
 // K the northern nodes; inv: A rows are the nodes, K the parity rows.
@@ -466,50 +487,17 @@ __global__ void split_table_kernel(const double* __restrict__ pnm, int ldp, int 
 
 int terms_of(int prec) { return (prec == SHT_BF16X2 || prec == SHT_FP16X2) ? 2 : 3; }
 
-cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* O,
-                        cudaStream_t s) {
-    const SplitTables* st = p->split;
-    GemmArgs g;
-    g.planes = inverse ? st->inv_planes : st->fwd_planes;
-    g.plane_bytes = (long long)(inverse ? st->inv_plane_bytes : st->fwd_plane_bytes);
-    g.probs = inverse ? st->d_probs_inv : st->d_probs_fwd;
-    g.tiles = inverse ? st->d_tiles_inv : st->d_tiles_fwd;
-    g.B = static_cast<const float*>(B);
-    g.O = static_cast<float*>(O);
-    g.C = 2 * p->F;
-    // rows of B are 16-byte aligned when C is a multiple of 4 floats
-    g.raw_bulk = ((g.C & 3) == 0) && (((uintptr_t)B & 15) == 0) ? 1 : 0;
-    g.status = p->d_status;
-    const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
-    if (ntiles == 0) return cudaSuccess;
-    if (st->terms == 3) {
-        cudaFuncSetAttribute(split_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg<3>::SMEM);
-        split_gemm_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(g);
-    } else {
-        cudaFuncSetAttribute(split_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg<2>::SMEM);
-        split_gemm_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(g);
-    }
-    return cudaGetLastError();
-}
-
-}  // namespace
-
-cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
-    if (p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3) {
-        set_error("FP16 split plans are not available in this build (BF16 only)");
-        return cudaErrorNotSupported;
-    }
-    SplitTables* st = new (std::nothrow) SplitTables();
-    if (!st) return cudaErrorMemoryAllocation;
-    p->split = st;
-    st->terms = terms_of(p->prec);
-    const int N = p->N, Jh = p->Jh, C = 2 * p->F;
+// Problems (one per (m, parity)) and tiles of both directions for
+// truncation N, Jh northern nodes and C real columns; tile.w = plan.
+void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& pf,
+                       std::vector<SplitProb>& pi, std::vector<int4>& tf,
+                       std::vector<int4>& ti, long long& fwd_bytes, long long& inv_bytes) {
     const int nprob = 2 * (N + 1);
-    std::vector<SplitProb> pf(nprob), pi(nprob);
-    std::vector<int4> tf, ti;
-    long long fwd_bytes = 0, inv_bytes = 0;
+    pf.assign(nprob, SplitProb{});
+    pi.assign(nprob, SplitProb{});
+    tf.clear();
+    ti.clear();
+    fwd_bytes = inv_bytes = 0;
     const int nct = (C + TN - 1) / TN;
     for (int m = 0; m <= N; ++m) {
         for (int q = 0; q < 2; ++q) {
@@ -528,7 +516,7 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
             f.o_stride = 2 * C;
             fwd_bytes += (long long)f.R8 * f.nkt * TK * 2;
             for (int mt = 0; mt * TM < R; ++mt)
-                for (int c = 0; c < nct; ++c) tf.push_back(make_int4(2 * m + q, mt, c, 0));
+                for (int c = 0; c < nct; ++c) tf.push_back(make_int4(2 * m + q, mt, c, plan));
             SplitProb& v = pi[2 * m + q];
             v.a_off = inv_bytes;
             v.R8 = (Jh + 7) / 8 * 8;
@@ -541,9 +529,61 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
             v.o_stride = C;
             inv_bytes += (long long)v.R8 * v.nkt * TK * 2;
             for (int mt = 0; mt * TM < Jh; ++mt)
-                for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, 0));
+                for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, plan));
         }
     }
+}
+
+GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* O) {
+    const SplitTables* st = p->split;
+    GemmArgs g;
+    g.planes = inverse ? st->inv_planes : st->fwd_planes;
+    g.plane_bytes = (long long)(inverse ? st->inv_plane_bytes : st->fwd_plane_bytes);
+    g.probs = inverse ? st->d_probs_inv : st->d_probs_fwd;
+    g.tiles = inverse ? st->d_tiles_inv : st->d_tiles_fwd;
+    g.B = static_cast<const float*>(B);
+    g.O = static_cast<float*>(O);
+    g.C = 2 * p->F;
+    // rows of B are 16-byte aligned when C is a multiple of 4 floats
+    g.raw_bulk = ((g.C & 3) == 0) && (((uintptr_t)B & 15) == 0) ? 1 : 0;
+    g.status = p->d_status;
+    return g;
+}
+
+cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* O,
+                        cudaStream_t s) {
+    const SplitTables* st = p->split;
+    const GemmArgs g = make_gemm_args(p, inverse, B, O);
+    const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
+    if (ntiles == 0) return cudaSuccess;
+    cudaError_t e;
+    if (st->terms == 3) {
+        if ((e = ensure_smem((const void*)split_gemm_kernel<3>, Cfg<3>::SMEM))) return e;
+        split_gemm_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(g);
+    } else {
+        if ((e = ensure_smem((const void*)split_gemm_kernel<2>, Cfg<2>::SMEM))) return e;
+        split_gemm_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
+    if (p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3) {
+        set_error("FP16 split plans are not available in this build (BF16 only)");
+        return cudaErrorNotSupported;
+    }
+    SplitTables* st = new (std::nothrow) SplitTables();
+    if (!st) return cudaErrorMemoryAllocation;
+    p->split = st;
+    st->terms = terms_of(p->prec);
+    const int N = p->N, Jh = p->Jh, C = 2 * p->F;
+    const int nprob = 2 * (N + 1);
+    std::vector<SplitProb> pf, pi;
+    std::vector<int4> tf, ti;
+    long long fwd_bytes = 0, inv_bytes = 0;
+    build_split_lists(N, Jh, C, 0, pf, pi, tf, ti, fwd_bytes, inv_bytes);
     st->fwd_plane_bytes = (size_t)(fwd_bytes + 255) / 256 * 256;
     st->inv_plane_bytes = (size_t)(inv_bytes + 255) / 256 * 256;
     st->ntiles_fwd = (int)tf.size();
@@ -590,6 +630,46 @@ void split_tables_destroy(sht_plan_s* p) {
         if (q) cudaFree(q);
     delete st;
     p->split = nullptr;
+}
+
+// Tiles of a group of split plans (same term count), heaviest first: every
+// tile's K loop has nkt steps.  Returns the host list.
+void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vector<int4>& out) {
+    std::vector<std::pair<int, int4>> all;
+    for (int q = 0; q < n; ++q) {
+        const sht_plan_s* p = plans[q];
+        std::vector<SplitProb> pf, pi;
+        std::vector<int4> tf, ti;
+        long long fb, ib;
+        build_split_lists(p->N, p->Jh, 2 * p->F, q, pf, pi, tf, ti, fb, ib);
+        const std::vector<SplitProb>& pr = inverse ? pi : pf;
+        for (const int4& t : inverse ? ti : tf) all.push_back({pr[t.x].nkt, t});
+    }
+    std::stable_sort(all.begin(), all.end(),
+                     [](const std::pair<int, int4>& a, const std::pair<int, int4>& b) {
+                         return a.first > b.first;
+                     });
+    out.clear();
+    for (auto& e : all) out.push_back(e.second);
+}
+
+cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
+                               const void* const* in, void* const* out, const int4* tiles,
+                               int ntiles, cudaStream_t s) {
+    if (ntiles == 0) return cudaSuccess;
+    GemmGroup G;
+    G.n = n;
+    G.tiles = tiles;
+    for (int q = 0; q < n; ++q) G.a[q] = make_gemm_args(plans[q], inverse, in[q], out[q]);
+    cudaError_t e;
+    if (plans[0]->split->terms == 3) {
+        if ((e = ensure_smem((const void*)split_gemm_group_kernel<3>, Cfg<3>::SMEM))) return e;
+        split_gemm_group_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(G);
+    } else {
+        if ((e = ensure_smem((const void*)split_gemm_group_kernel<2>, Cfg<2>::SMEM))) return e;
+        split_gemm_group_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(G);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_legendre_fwd_split(const sht_plan_s* p, const void* work, void* spec,

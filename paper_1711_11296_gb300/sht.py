@@ -150,6 +150,61 @@ class Plan:
             pass
 
 
+class Group:
+    """Several plans transformed by one launch per kernel stage.
+
+    ``forward(grids)`` / ``inverse(specs)`` take and return lists with one
+    tensor per plan (each plan's own layouts).  The plans must outlive the
+    group."""
+
+    def __init__(self, plans):
+        plans = list(plans)
+        if not 1 <= len(plans) <= 8:
+            raise ValueError("a group holds 1..8 plans")
+        self.plans = plans
+        arr = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(plans[0].device):
+            check(lib.sht_group_create(arr, len(plans), ctypes.byref(h)))
+        self._h = h
+
+    def _ptrs(self, ts):
+        return (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+    def forward(self, grids, out=None):
+        if len(grids) != len(self.plans):
+            raise ValueError("one grid per plan")
+        out = [p.empty_spec() for p in self.plans] if out is None else out
+        for p, g, o in zip(self.plans, grids, out):
+            p._check(g, (p.F, p.J, p.I), p.real_dtype, "grid")
+            p._check(o, (p.ncoef, p.F), p.complex_dtype, "spec")
+        check(lib.sht_group_forward(self._h, self._ptrs(grids), self._ptrs(out),
+                                    _stream_ptr(self.plans[0].device)))
+        return out
+
+    def inverse(self, specs, out=None):
+        if len(specs) != len(self.plans):
+            raise ValueError("one spectrum per plan")
+        out = [p.empty_grid() for p in self.plans] if out is None else out
+        for p, a, o in zip(self.plans, specs, out):
+            p._check(a, (p.ncoef, p.F), p.complex_dtype, "spec")
+            p._check(o, (p.F, p.J, p.I), p.real_dtype, "grid")
+        check(lib.sht_group_inverse(self._h, self._ptrs(specs), self._ptrs(out),
+                                    _stream_ptr(self.plans[0].device)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.sht_group_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Analysis(torch.autograd.Function):
     """grid -> spectrum with the native adjoint as backward."""
 
@@ -184,4 +239,5 @@ def synthesis(spec, plan):
     return Synthesis.apply(spec, plan)
 
 
-__all__ = ["Plan", "Analysis", "Synthesis", "analysis", "synthesis", "SHTError"]
+__all__ = ["Plan", "Group", "Analysis", "Synthesis", "analysis", "synthesis",
+           "SHTError"]
