@@ -44,9 +44,9 @@ struct DeviceGuard {
     }
 };
 
-bool factor_fft(int L, FftShape& sh) {
+bool factor_fft(int L, bool fp64, FftShape& sh) {
     if (!fft_factorable(L)) return false;
-    sh = fft_factor(L);
+    sh = fft_factor(L, fp64);
     return true;
 }
 
@@ -169,13 +169,15 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
         return SHT_ERR_ARG;
     }
     FftShape shape;
-    if (!factor_fft(I / 2, shape)) {
+    if (!factor_fft(I / 2, precision == SHT_FP64, shape)) {
         set_error("I/2 = %d has prime factors other than 2, 3, 5", I / 2);
         return SHT_ERR_ARG;
     }
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "no CUDA device");
+    e = fft_constants_init();
+    if (e != cudaSuccess) return cuda_fail(e, "FFT constants");
 
     sht_plan_s* p = new (std::nothrow) sht_plan_s();
     if (!p) { set_error("host allocation failed"); return SHT_ERR_ALLOC; }
@@ -196,7 +198,7 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
     if (g > 16) g = 16;
     if (g > nfields) g = nfields;
     p->G = (int)g;
-    p->fft_threads = 512;
+    p->fft_threads = 256;
     p->fft_smem = fft_smem_bytes(I, p->G, fp64);
     if (p->fft_smem > 227 * 1024) {
         delete p;

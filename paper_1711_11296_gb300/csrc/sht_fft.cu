@@ -30,12 +30,16 @@
 // digit reversal are constants, so the index arithmetic needs no integer
 // division by a runtime value.  Other lengths use the same code with the
 // shape read at run time.
+#include <math.h>
+
+#include <mutex>
+
 #include "sht_internal.h"
 
 namespace sht {
 namespace {
 
-constexpr int NT = 512;   // threads per FFT CTA (two CTAs per SM)
+constexpr int NT = 256;   // threads per FFT CTA (two CTAs per SM for FP32)
 
 template <typename T> struct C2 {
     using V = typename Vec2<T>::type;
@@ -54,9 +58,23 @@ template <typename T> struct C2 {
 };
 
 // The plan's factorisation as a compile-time constant.
-template <int L> struct FacOf {
-    static constexpr FftShape v = fft_factor(L);
+template <int L, bool FP64> struct FacOf {
+    static constexpr FftShape v = fft_factor(L, FP64);
 };
+
+// W_N^e = exp(-2 pi i e/N) for the composite register DFT sizes, written
+// once per device by fft_constants_init (offsets per N below).
+constexpr int kTw10 = 0, kTw16 = 10, kTw20 = 26, kTw32 = 46, kTw40 = 78, kTwTotal = 118;
+__constant__ float2 c_twf[kTwTotal];
+__constant__ double2 c_twd[kTwTotal];
+
+template <typename T>
+__device__ __forceinline__ typename Vec2<T>::type twc(int idx) {
+    if constexpr (sizeof(T) == 4)
+        return c_twf[idx];
+    else
+        return c_twd[idx];
+}
 
 template <typename T>
 __device__ __forceinline__ int ph(int pos) {
@@ -68,6 +86,7 @@ template <typename T, int R> struct Dft;
 
 template <typename T> struct Dft<T, 2> {
     using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return k; }
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         const V y0 = K::add(a[0], a[1]);
@@ -78,6 +97,7 @@ template <typename T> struct Dft<T, 2> {
 
 template <typename T> struct Dft<T, 3> {
     using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return k; }
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         const T h = (T)0.86602540378443864676;   // sin(2 pi/3)
@@ -93,6 +113,7 @@ template <typename T> struct Dft<T, 3> {
 
 template <typename T> struct Dft<T, 4> {
     using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return k; }
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         const V s02 = K::add(a[0], a[2]), d02 = K::sub(a[0], a[2]);
@@ -106,6 +127,7 @@ template <typename T> struct Dft<T, 4> {
 
 template <typename T> struct Dft<T, 8> {
     using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return k; }
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         const T r = (T)0.70710678118654752440;   // 1/sqrt(2)
@@ -131,6 +153,7 @@ template <typename T> struct Dft<T, 8> {
 
 template <typename T> struct Dft<T, 5> {
     using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return k; }
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         // cos/sin of 2 pi/5 and 4 pi/5
@@ -153,6 +176,49 @@ template <typename T> struct Dft<T, 5> {
     }
 };
 
+// Composite DFT of size N = A B in registers, in place:
+//   X[k1 + A k2] = sum_b W_B^{b k2} W_N^{b k1} sum_a x[b + B a] W_A^{a k1},
+// i.e. B DFTs of size A over stride-B subsequences (results written back to
+// the same registers), the twiddles W_N^{b k1} (constant memory), then A
+// DFTs of size B over each contiguous block of B.  X[k] is left in
+// register pos(k) = k1 B + k2 (k = k1 + A k2); the butterfly stores with
+// this map, so no register array beyond the input is live.
+template <typename T, int A, int B, int TWOFF>
+struct DftComposite {
+    using V = typename Vec2<T>::type;
+    static __device__ __forceinline__ constexpr int pos(int k) { return (k % A) * B + k / A; }
+    static __device__ __forceinline__ void run(V* x) {
+        using K = C2<T>;
+        constexpr int N = A * B;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            V t[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) t[a] = x[b + B * a];
+            Dft<T, A>::run(t);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1)
+                x[b + B * k1] =
+                    (b * k1 == 0) ? t[k1] : K::mul(t[k1], twc<T>(TWOFF + (b * k1) % N));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) {
+            V t[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) t[b] = x[k1 * B + b];
+            Dft<T, B>::run(t);
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) x[k1 * B + k2] = t[k2];
+        }
+    }
+};
+
+template <typename T> struct Dft<T, 10> : DftComposite<T, 2, 5, kTw10> {};
+template <typename T> struct Dft<T, 16> : DftComposite<T, 4, 4, kTw16> {};
+template <typename T> struct Dft<T, 20> : DftComposite<T, 4, 5, kTw20> {};
+template <typename T> struct Dft<T, 32> : DftComposite<T, 8, 4, kTw32> {};
+template <typename T> struct Dft<T, 40> : DftComposite<T, 8, 5, kTw40> {};
+
 // One DIF butterfly of radix R: reads z[base + t M], t < R, applies the
 // radix-R DFT, multiplies output k1 by W_S^{n1 k1} (per-pass table entry
 // (k1 - 1) M + n1) and writes it back to z[base + k1 M].
@@ -162,19 +228,18 @@ __device__ __forceinline__ void bfly(typename Vec2<T>::type* z, int base, int M,
     using V = typename Vec2<T>::type;
     using K = C2<T>;
     V a[R];
-    int id[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-        id[t] = ph<T>(base + t * M);
-        a[t] = z[id[t]];
-    }
+    for (int t = 0; t < R; ++t) a[t] = z[ph<T>(base + t * M)];
     Dft<T, R>::run(a);
+    // output k1 sits in register pos(k1)
     if (n1 != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < R; ++k1) a[k1] = K::mul(a[k1], tw[(k1 - 1) * M + n1]);
+        for (int k1 = 1; k1 < R; ++k1) {
+            a[Dft<T, R>::pos(k1)] = K::mul(a[Dft<T, R>::pos(k1)], tw[(k1 - 1) * M + n1]);
+        }
     }
 #pragma unroll
-    for (int t = 0; t < R; ++t) z[id[t]] = a[t];
+    for (int k1 = 0; k1 < R; ++k1) z[ph<T>(base + k1 * M)] = a[Dft<T, R>::pos(k1)];
 }
 
 // In-place mixed-radix DIF FFT over `nrows` padded rows (pitch LP), shape
@@ -197,6 +262,16 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
             const int n1 = b - blk * M;
             auto* z = rows + (size_t)row * LP;
             const int base = blk * S + n1;
+            if constexpr (sizeof(T) == 4) {   // two-pass shapes (FP32 only)
+                if (r > 8) {
+                    if (r == 10) bfly<T, 10>(z, base, M, tw, n1);
+                    else if (r == 16) bfly<T, 16>(z, base, M, tw, n1);
+                    else if (r == 20) bfly<T, 20>(z, base, M, tw, n1);
+                    else if (r == 32) bfly<T, 32>(z, base, M, tw, n1);
+                    else bfly<T, 40>(z, base, M, tw, n1);
+                    continue;
+                }
+            }
             if (r == 8)
                 bfly<T, 8>(z, base, M, tw, n1);
             else if (r == 4)
@@ -216,7 +291,7 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
 template <typename T, int L, int P>
 __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int nrows, int LP,
                                              const typename Vec2<T>::type* twp) {
-    constexpr FftShape F = FacOf<L>::v;
+    constexpr FftShape F = FacOf<L, sizeof(T) == 8>::v;
     if constexpr (P < F.npass) {
         constexpr int R = F.radix[P];
         constexpr int M = F.span[P];
@@ -237,9 +312,9 @@ __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int n
 }
 
 // Digit-reversed position of frequency k.
-template <int L>
+template <typename T, int L>
 __device__ __forceinline__ int rev_fixed(int k) {
-    constexpr FftShape F = FacOf<L>::v;
+    constexpr FftShape F = FacOf<L, sizeof(T) == 8>::v;
     int pos = 0;
 #pragma unroll
     for (int q = 0; q < F.npass; ++q) {
@@ -294,10 +369,10 @@ __device__ __forceinline__ void run_passes(typename Vec2<T>::type* rows, int nro
         passes_runtime<T>(rows, nrows, LP, sh, twp);
 }
 
-template <int LT>
+template <typename T, int LT>
 __device__ __forceinline__ int rev_of(int k, const int* rev) {
     if constexpr (LT > 0)
-        return rev_fixed<LT>(k);
+        return rev_fixed<T, LT>(k);
     else
         return rev[k];
 }
@@ -344,7 +419,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
                (long long)j * A.src.row_stride;
     };
 
-    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT>::v.twtotal : A.shape.twtotal);
+    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     {
         // element k of row r goes to rows[r LP + ph(k)]; eight loads in flight
         const int s = A.src.elem_stride;
@@ -379,8 +454,8 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     for (Walk2 w(tid, nf); w.major * nf + w.minor < nout; w.next()) {
         const int m = w.major;
         const int fl = w.minor;
-        const int pm = ph<T>(rev_of<LT>(m, A.rev));
-        const int pc = ph<T>(rev_of<LT>(m == 0 ? 0 : L - m, A.rev));
+        const int pm = ph<T>(rev_of<T, LT>(m, A.rev));
+        const int pc = ph<T>(rev_of<T, LT>(m == 0 ? 0 : L - m, A.rev));
         const V wt = A.twpost[m];
         auto real_spec = [&](const V* z) -> V {
             const V zm = z[pm];
@@ -426,7 +501,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     const int nrows = equator ? nf : 2 * nf;
     const int tid = threadIdx.x;
 
-    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT>::v.twtotal : A.shape.twtotal);
+    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     // unfold S/A into the two hemispheres' zonal spectra Y_m, m <= N
     // (four loads in flight per thread)
     const int nin = (A.N + 1) * nf;
@@ -498,7 +573,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
         V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I);
-        const V v = rows[(size_t)r * LP + ph<T>(rev_of<LT>(k, A.rev))];
+        const V v = rows[(size_t)r * LP + ph<T>(rev_of<T, LT>(k, A.rev))];
         xv[k] = K::make(v.x * rs, -v.y * rs);
     }
 }
@@ -688,6 +763,32 @@ cudaError_t inv_group_impl(sht_plan_s* const* plans, int n, void* const* grids,
 }
 
 }  // namespace
+
+cudaError_t fft_constants_init() {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    float2 hf[kTwTotal];
+    double2 hd[kTwTotal];
+    const int sizes[5] = {10, 16, 20, 32, 40};
+    const int offs[5] = {kTw10, kTw16, kTw20, kTw32, kTw40};
+    const long double pi = 3.14159265358979323846264338327950288L;
+    for (int q = 0; q < 5; ++q)
+        for (int k = 0; k < sizes[q]; ++k) {
+            const long double ang = 2.0L * pi * (long double)k / (long double)sizes[q];
+            const double c = (double)cosl(ang), sn = -(double)sinl(ang);
+            hd[offs[q] + k] = make_double2(c, sn);
+            hf[offs[q] + k] = make_float2((float)c, (float)sn);
+        }
+    e = cudaMemcpyToSymbol(c_twf, hf, sizeof(hf));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_twd, hd, sizeof(hd));
+    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+    return e;
+}
 
 cudaError_t launch_fft_forward_group(sht_plan_s* const* plans, int n,
                                      const void* const* grids, cudaStream_t s) {

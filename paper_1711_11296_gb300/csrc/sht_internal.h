@@ -43,7 +43,7 @@ struct FftShape {
 // that neither the power-of-two strides of the passes and of the
 // digit-reversed reads nor the row-to-row distance map onto one bank.
 template <typename T> struct PadShift;
-template <> struct PadShift<float> { static constexpr int value = 4; };    // 8-byte complex
+template <> struct PadShift<float> { static constexpr int value = 5; };    // 8-byte complex
 template <> struct PadShift<double> { static constexpr int value = 3; };   // 16-byte complex
 
 inline int fft_row_pitch(int L, bool fp64) {
@@ -146,14 +146,27 @@ cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
 cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
 
+// Register DFT sizes of the two-pass FP32 FFT (L = Q x 32).
+__host__ __device__ constexpr bool fft_big_radix(int q) {
+    return q == 2 || q == 4 || q == 8 || q == 10 || q == 16 || q == 20 || q == 32 ||
+           q == 40;
+}
+
 // Mixed-radix factorisation of the half-length FFT, shared by the plans,
-// the allocation-free entry point and the compile-time kernels: radices 8
-// first (fewest shared-memory passes), then 4, 2, 3, 5; spans and per-pass
-// twiddle offsets follow.  npass = 0 and L != 1 means "not factorable".
-__host__ __device__ constexpr FftShape fft_factor(int L) {
+// the allocation-free entry point and the compile-time kernels.  FP32
+// transforms of L = Q x 32 (Q a register DFT size) use two passes, radix Q
+// then radix 32, each butterfly computed in registers; everything else
+// uses radices 8 first, then 4, 2, 3, 5.  Spans and per-pass twiddle
+// offsets follow.  npass = 0 and L != 1 means "not factorable".
+__host__ __device__ constexpr FftShape fft_factor(int L, bool fp64) {
     FftShape sh{};
     sh.L = L;
     int rest = L, np = 0;
+    if (!fp64 && L % 32 == 0 && fft_big_radix(L / 32)) {
+        sh.radix[np++] = L / 32;
+        sh.radix[np++] = 32;
+        rest = 1;
+    }
     const int cand[5] = {8, 4, 2, 3, 5};
     for (int c = 0; c < 5; ++c)
         while (rest % cand[c] == 0 && np < kMaxRadixPasses) {
@@ -174,8 +187,12 @@ __host__ __device__ constexpr FftShape fft_factor(int L) {
 }
 
 __host__ __device__ constexpr bool fft_factorable(int L) {
-    return L == 1 || fft_factor(L).npass > 0;
+    return L == 1 || fft_factor(L, true).npass > 0;
 }
+
+// Write the constant twiddles of the register DFTs to the current device
+// (once per device; safe to call repeatedly).
+cudaError_t fft_constants_init();
 
 // FFT launches
 cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,

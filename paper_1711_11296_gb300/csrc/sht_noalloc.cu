@@ -83,7 +83,7 @@ __global__ void rev_kernel(FftShape sh, int* rev) {
 
 bool factor(int L, FftShape& sh) {
     if (!fft_factorable(L)) return false;
-    sh = fft_factor(L);
+    sh = fft_factor(L, true);
     return true;
 }
 
@@ -124,7 +124,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     long g = (long)((budget / rowbytes > 1 ? budget / rowbytes - 1 : 0) / 2);
     g = g < 1 ? 1 : (g > 16 ? 16 : g);
     t.G = (int)(g > nfields ? nfields : g);
-    t.fft_threads = 512;
+    t.fft_threads = 256;
     t.fft_smem = fft_smem_bytes(I, t.G, true);
     if (t.fft_smem > 227 * 1024) {
         set_error("I = %d too large for the shared-memory FFT", I);
