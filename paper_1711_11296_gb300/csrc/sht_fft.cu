@@ -19,8 +19,9 @@
 // PadShift (element pos at pos + (pos >> s), odd row pitch), which keeps the
 // passes' power-of-two strides, the digit-reversed accesses and the
 // row-to-row distance off a single bank; each pass reads its twiddles from
-// a table contiguous in the butterfly index.  Global loads are issued eight
-// per thread before their stores so that their latencies overlap.  The
+// a table contiguous in the butterfly index.  Global loads are
+// asynchronous element copies (cp.async) straight into the padded layout,
+// all in flight before the CTA waits once.  The
 // CTAs of all field groups of one latitude are adjacent in the launch
 // order, so their partial-sector writes of the same workspace rows meet in
 // L2.
@@ -74,6 +75,22 @@ __device__ __forceinline__ typename Vec2<T>::type twc(int idx) {
         return c_twf[idx];
     else
         return c_twd[idx];
+}
+
+// Asynchronous global -> shared copy of one element (cp.async, no register
+// staging, so all of a thread's copies are in flight at once).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 template <typename T>
@@ -421,30 +438,20 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
 
     load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     {
-        // element k of row r goes to rows[r LP + ph(k)]; eight loads in flight
+        // element k of row r goes to rows[r LP + ph(k)], copied
+        // asynchronously so that all of the CTA's loads are in flight
         const int s = A.src.elem_stride;
-        Walk2 w(tid, L);   // (row, k)
-        while (w.major < nrows) {
-            V v[8];
-            int rr[8], kk[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                rr[u] = w.major;
-                kk[u] = w.minor;
-                if (w.major < nrows) {
-                    const T* x = row_ptr(w.major);
-                    if (!STRIDED)
-                        v[u] = reinterpret_cast<const V*>(x)[w.minor];
-                    else
-                        v[u] = K::make(x[(long long)(2 * w.minor) * s],
-                                       x[(long long)(2 * w.minor + 1) * s]);
-                }
-                w.next();
+        for (Walk2 w(tid, L); w.major < nrows; w.next()) {
+            const T* x = row_ptr(w.major);
+            V* d = rows + (size_t)w.major * LP + ph<T>(w.minor);
+            if (!STRIDED) {
+                cp_async<sizeof(V)>(d, reinterpret_cast<const V*>(x) + w.minor);
+            } else {
+                cp_async<sizeof(T)>(&d->x, x + (long long)(2 * w.minor) * s);
+                cp_async<sizeof(T)>(&d->y, x + (long long)(2 * w.minor + 1) * s);
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (rr[u] < nrows) rows[(size_t)rr[u] * LP + ph<T>(kk[u])] = v[u];
         }
+        cp_async_wait_all();
     }
     __syncthreads();
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
@@ -503,66 +510,60 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
 
     load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     // unfold S/A into the two hemispheres' zonal spectra Y_m, m <= N
-    // (four loads in flight per thread)
+    // (S lands in the northern row, A in the southern one, copied
+    // asynchronously; then both hemispheres are formed in place)
     const int nin = (A.N + 1) * nf;
-    {
-        Walk2 w(tid, nf);   // (m, field)
-        while (w.major * nf + w.minor < nin) {
-            V Sv[4], Av[4];
-            int mm[4], ff[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                mm[u] = w.major;
-                ff[u] = w.minor;
-                if (w.major * nf + w.minor < nin) {
-                    const size_t base = ((size_t)w.major * 2 * A.Jh + jh) * A.F + f0 + w.minor;
-                    Sv[u] = A.work[base];
-                    Av[u] = equator ? K::make((T)0, (T)0) : A.work[base + (size_t)A.Jh * A.F];
-                }
-                w.next();
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int m = mm[u], fl = ff[u];
-                if (m * nf + fl >= nin) continue;
-                const T fac = (T)(m == 0 ? 1.0 : A.mfactor1);
-                V yn = K::scale(K::add(Sv[u], Av[u]), fac);
-                V ys = K::scale(K::sub(Sv[u], Av[u]), fac);
-                if (m == 0) {
-                    yn.y = (T)0;
-                    ys.y = (T)0;
-                }
-                rows[(size_t)fl * LP + ph<T>(m)] = yn;
-                if (!equator) rows[(size_t)(nf + fl) * LP + ph<T>(m)] = ys;
-            }
-        }
+    for (Walk2 w(tid, nf); w.major * nf + w.minor < nin; w.next()) {
+        const int m = w.major, fl = w.minor;
+        const size_t base = ((size_t)m * 2 * A.Jh + jh) * A.F + f0 + fl;
+        cp_async<sizeof(V)>(rows + (size_t)fl * LP + ph<T>(m), A.work + base);
+        if (!equator)
+            cp_async<sizeof(V)>(rows + (size_t)(nf + fl) * LP + ph<T>(m),
+                                A.work + base + (size_t)A.Jh * A.F);
     }
-    const int nz = L - (A.N + 1);
-    if (nz > 0) {
-        for (Walk2 w(tid, nz); w.major < nrows; w.next())
-            rows[(size_t)w.major * LP + ph<T>(A.N + 1 + w.minor)] = K::make((T)0, (T)0);
-    }
+    cp_async_wait_all();
     __syncthreads();
-    // Hermitian packing into conj(Z), pairs (q, L-q) owned by one thread
+    // One thread owns frequencies (q, L-q) of field fl in both hemispheres:
+    // Y_m = fac (S_m +- A_m) (Y_0 real, Y_m = 0 for m > N; stale slots beyond
+    // N are never read), then the Hermitian packing
+    //   Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q}),
+    // stored as conj(Z) in place.
     const int half = L / 2;
-    for (Walk2 w(tid, half + 1); w.major < nrows; w.next()) {
-        const int q = w.minor;
+    const int N = A.N;
+    for (Walk2 w(tid, half + 1); w.major < nf; w.next()) {
+        const int fl = w.major, q = w.minor;
         const int qc = L - q;
         if (q > qc) continue;
-        V* z = rows + (size_t)w.major * LP;
-        const V yq = z[ph<T>(q)];
-        const V yc = (q == 0) ? K::make((T)0, (T)0) : z[ph<T>(qc)];
-        // Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q})
+        V* zn = rows + (size_t)fl * LP;
+        V* zs = rows + (size_t)(nf + fl) * LP;
+        auto yval = [&](const V* z, const V* za, int m, bool south) -> V {
+            if (m > N || m >= L) return K::make((T)0, (T)0);
+            const V S = z[ph<T>(m)];
+            const V Asym = equator ? K::make((T)0, (T)0) : za[ph<T>(m)];
+            const T fac = (T)(m == 0 ? 1.0 : A.mfactor1);
+            V y = south ? K::scale(K::sub(S, Asym), fac) : K::scale(K::add(S, Asym), fac);
+            if (m == 0) y.y = (T)0;
+            return y;
+        };
+        const int qcm = (q == 0) ? L : qc;   // Y_L = 0
+        const V ynq = yval(zn, zs, q, false), ync = yval(zn, zs, qcm, false);
+        V ysq = K::make((T)0, (T)0), ysc = K::make((T)0, (T)0);
+        if (!equator) {
+            ysq = yval(zn, zs, q, true);
+            ysc = yval(zn, zs, qcm, true);
+        }
         const V wq = K::conj(A.twpost[q]);
-        const V zq = K::add(K::add(yq, K::conj(yc)),
-                            K::mul_pi(K::mul(wq, K::sub(yq, K::conj(yc)))));
+        auto pack = [&](V y, V yc, V wv) -> V {
+            return K::conj(K::add(K::add(y, K::conj(yc)),
+                                  K::mul_pi(K::mul(wv, K::sub(y, K::conj(yc))))));
+        };
+        zn[ph<T>(q)] = pack(ynq, ync, wq);
+        if (!equator) zs[ph<T>(q)] = pack(ysq, ysc, wq);
         if (q != 0 && q != qc) {
             const V wc = K::conj(A.twpost[qc]);
-            const V zc = K::add(K::add(yc, K::conj(yq)),
-                                K::mul_pi(K::mul(wc, K::sub(yc, K::conj(yq)))));
-            z[ph<T>(qc)] = K::conj(zc);
+            zn[ph<T>(qc)] = pack(ync, ynq, wc);
+            if (!equator) zs[ph<T>(qc)] = pack(ysc, ysq, wc);
         }
-        z[ph<T>(q)] = K::conj(zq);
     }
     __syncthreads();
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
