@@ -186,6 +186,8 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
     p->Jh = (J + 1) / 2;
     p->M = N + 1;
     p->device = dev;
+    p->num_sms = 148;
+    cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev);
     p->ncoef = (size_t)(N + 1) * (N + 2) / 2;
     p->ldp = (p->Jh + 7) / 8 * 8;
     p->fft = shape;

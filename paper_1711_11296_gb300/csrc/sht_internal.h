@@ -94,6 +94,7 @@ struct sht_plan_s {
     int Jh;          // (J+1)/2 northern nodes incl. the Equator
     int M;           // N+1 zonal wavenumbers
     int device;
+    int num_sms;     // SMs of the device (grid of the persistent kernels)
     size_t ncoef;
     int ldp;         // leading dimension of the P~ table (>= Jh)
     int G;           // fields per FFT CTA
