@@ -441,14 +441,16 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
         // element k of row r goes to rows[r LP + ph(k)], copied
         // asynchronously so that all of the CTA's loads are in flight
         const int s = A.src.elem_stride;
-        for (Walk2 w(tid, L); w.major < nrows; w.next()) {
-            const T* x = row_ptr(w.major);
-            V* d = rows + (size_t)w.major * LP + ph<T>(w.minor);
-            if (!STRIDED) {
-                cp_async<sizeof(V)>(d, reinterpret_cast<const V*>(x) + w.minor);
-            } else {
-                cp_async<sizeof(T)>(&d->x, x + (long long)(2 * w.minor) * s);
-                cp_async<sizeof(T)>(&d->y, x + (long long)(2 * w.minor + 1) * s);
+        for (int r = 0; r < nrows; ++r) {
+            const T* x = row_ptr(r);
+            V* d = rows + (size_t)r * LP;
+            for (int k = tid; k < L; k += NT) {
+                if (!STRIDED) {
+                    cp_async<sizeof(V)>(d + ph<T>(k), reinterpret_cast<const V*>(x) + k);
+                } else {
+                    cp_async<sizeof(T)>(&d[ph<T>(k)].x, x + (long long)(2 * k) * s);
+                    cp_async<sizeof(T)>(&d[ph<T>(k)].y, x + (long long)(2 * k + 1) * s);
+                }
             }
         }
         cp_async_wait_all();
@@ -569,13 +571,15 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
     const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
-    for (Walk2 w(tid, L); w.major < nrows; w.next()) {
-        const int r = w.major, k = w.minor;
+    for (int r = 0; r < nrows; ++r) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
         V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I);
-        const V v = rows[(size_t)r * LP + ph<T>(rev_of<T, LT>(k, A.rev))];
-        xv[k] = K::make(v.x * rs, -v.y * rs);
+        const V* z = rows + (size_t)r * LP;
+        for (int k = tid; k < L; k += NT) {
+            const V v = z[ph<T>(rev_of<T, LT>(k, A.rev))];
+            xv[k] = K::make(v.x * rs, -v.y * rs);
+        }
     }
 }
 
