@@ -158,13 +158,10 @@ def fft_bytes(w, F, real_bytes):
 # DRAM traffic per launch of the kernels that dominate a step, from ncu
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel
 # code on the T319 x 64 field-level case, scaled by grid points x
-# field-levels (15.99x to T639 x 256).  Writes still held in L2 when a
-# launch ends are not counted by the capture.  Keyed by (stage, path,
-# workload, field-levels); any kernel change invalidates the entry.
-MEASURED_TRAFFIC = {
-    ("fft_inverse", "bf16x3", "T639", 256): (105.09e6 + 151.65e6) * 15.99,
-    ("fft_forward", "bf16x3", "T639", 256): (210.21e6 + 71.01e6) * 15.99,
-}
+# field-levels.  Writes still held in L2 when a launch ends are not counted
+# by the capture.  Keyed by (stage, path, workload, field-levels); an entry
+# is removed whenever its kernel changes and re-added from a new capture.
+MEASURED_TRAFFIC = {}
 
 
 def peaks():
