@@ -259,8 +259,8 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 def split_gemm_bytes(w, F, prec, inverse):
     """Algorithmic HBM bytes of one split Legendre launch: the FP32 operand
-    read once, the BF16 term planes of the P table read once (rows padded to
-    8, K to 32), the FP32 result written once."""
+    read once, the 16-bit term planes of the P table read once (rows padded
+    to 8, K to 16), the FP32 result written once."""
     terms = 2 if prec.endswith("x2") else 3
     Jh = (w.J + 1) // 2
     C = 2 * F
@@ -273,9 +273,9 @@ def split_gemm_bytes(w, F, prec, inverse):
             d = w.N - m - q
             R = d // 2 + 1 if d >= 0 else 0
             if inverse:
-                tab += ((Jh + 7) // 8 * 8) * ((R + 31) // 32 * 32) * 2
+                tab += ((Jh + 7) // 8 * 8) * ((R + 15) // 16 * 16) * 2
             elif R:
-                tab += ((R + 7) // 8 * 8) * ((Jh + 31) // 32 * 32) * 2
+                tab += ((R + 7) // 8 * 8) * ((Jh + 15) // 16 * 16) * 2
     tab *= terms
     return (spec + tab + work)
 
@@ -291,7 +291,9 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (no measured "
                                "FP64 peak in MEASURED_PEAKS.json)"}
     elif name.startswith("legendre"):
-        products = 3 if prec.endswith("x2") else 6
+        # tensor-core products per split: x_a y_b with a + b < terms, less
+        # x_2 y_2 for FP16 (weight 2^-22)
+        products = {"bf16x2": 3, "fp16x2": 3, "bf16x3": 6, "fp16x3": 5}[prec]
         fl = legendre_flops(w, F) * products
         by = split_gemm_bytes(w, F, prec, name.endswith("inverse"))
         t_frac = fl / per_launch_s / 1e12 / pk["bf16_tflops_sustained"]

@@ -50,6 +50,13 @@ typedef enum {
     SHT_FP16X2 = 3, /* FP32 FFT; Legendre as 2-term FP16 split products  */
     SHT_FP16X3 = 4  /* FP32 FFT; Legendre as 3-term FP16 split products  */
 } sht_precision;
+/* FP16 splits scale each row of the P~ table (at plan time) and each real
+ * column of the FP32 operand (per call, from its largest magnitude) by a
+ * power of two into [-1, 1), so that the narrow FP16 exponent range holds
+ * the operands; x = x_1 + 2^-11 (x_2 [+ x_3]).  FP16x2 keeps ~22 bits of
+ * each operand with 3 products, FP16x3 ~33 bits with 5 products; both
+ * drop x_2 y_2 (weight 2^-22).  Errors are relative to the row and column
+ * maxima rather than to each element. */
 
 typedef enum {
     SHT_OK = 0,

@@ -352,6 +352,7 @@ struct FwdArgs {
     const int* rev;
     const double* rowscale;
     double mscale0, mscale1;
+    unsigned* colmax;   // FP16 split plans: max |output| per real column (float bits)
     int F, J, Jh, L, LP, N, G;
     FftShape shape;
 };
@@ -460,6 +461,23 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
 
     const int nout = (A.N + 1) * nf;
     const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
+    // column maxima of the output (real and imaginary part of each field),
+    // gathered per thread while its field stays the same, then per CTA in
+    // shared memory, then one global atomic per column and CTA
+    const bool track = A.colmax != nullptr;
+    unsigned* smax = reinterpret_cast<unsigned*>(tws + (LT > 0 ? LT : A.L));
+    if (track) {
+        for (int e = tid; e < 2 * nf; e += NT) smax[e] = 0u;
+        __syncthreads();
+    }
+    float mre = 0.f, mim = 0.f;
+    int mcur = -1;
+    auto flush = [&]() {
+        if (mcur >= 0) {
+            atomicMax(&smax[2 * mcur], __float_as_uint(mre));
+            atomicMax(&smax[2 * mcur + 1], __float_as_uint(mim));
+        }
+    };
     for (Walk2 w(tid, nf); w.major * nf + w.minor < nout; w.next()) {
         const int m = w.major;
         const int fl = w.minor;
@@ -485,8 +503,23 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
         }
         const T sc = (T)0.5 * rs * (T)(m == 0 ? A.mscale0 : A.mscale1);
         const size_t base = ((size_t)m * 2 * A.Jh + jh) * A.F + f0 + fl;
-        A.work[base] = K::scale(S, sc);
-        A.work[base + (size_t)A.Jh * A.F] = K::scale(Asym, sc);
+        const V os = K::scale(S, sc), oa = K::scale(Asym, sc);
+        A.work[base] = os;
+        A.work[base + (size_t)A.Jh * A.F] = oa;
+        if (track) {
+            if (fl != mcur) {
+                flush();
+                mcur = fl;
+                mre = mim = 0.f;
+            }
+            mre = fmaxf(mre, fmaxf(fabsf((float)os.x), fabsf((float)oa.x)));
+            mim = fmaxf(mim, fmaxf(fabsf((float)os.y), fabsf((float)oa.y)));
+        }
+    }
+    if (track) {
+        flush();
+        __syncthreads();
+        for (int e = tid; e < 2 * nf; e += NT) atomicMax(&A.colmax[2 * f0 + e], smax[e]);
     }
 }
 
@@ -534,37 +567,33 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     const int N = A.N;
     for (Walk2 w(tid, half + 1); w.major < nf; w.next()) {
         const int fl = w.major, q = w.minor;
-        const int qc = L - q;
-        if (q > qc) continue;
+        const int qc = L - q;   // >= q, as q <= L/2
         V* zn = rows + (size_t)fl * LP;
         V* zs = rows + (size_t)(nf + fl) * LP;
-        auto yval = [&](const V* z, const V* za, int m, bool south) -> V {
-            if (m > N || m >= L) return K::make((T)0, (T)0);
-            const V S = z[ph<T>(m)];
-            const V Asym = equator ? K::make((T)0, (T)0) : za[ph<T>(m)];
-            const T fac = (T)(m == 0 ? 1.0 : A.mfactor1);
-            V y = south ? K::scale(K::sub(S, Asym), fac) : K::scale(K::add(S, Asym), fac);
-            if (m == 0) y.y = (T)0;
-            return y;
-        };
-        const int qcm = (q == 0) ? L : qc;   // Y_L = 0
-        const V ynq = yval(zn, zs, q, false), ync = yval(zn, zs, qcm, false);
-        V ysq = K::make((T)0, (T)0), ysc = K::make((T)0, (T)0);
-        if (!equator) {
-            ysq = yval(zn, zs, q, true);
-            ysc = yval(zn, zs, qcm, true);
-        }
+        const V zero = K::make((T)0, (T)0);
+        const int pq = ph<T>(q), pc = ph<T>(qc);
+        // S and A at frequencies q and L - q, each read once (zero above N;
+        // Y_L = 0 for q = 0)
+        const bool hq = q <= N, hc = q != 0 && qc <= N;
+        const V Sq = hq ? zn[pq] : zero;
+        const V Aq = (hq && !equator) ? zs[pq] : zero;
+        const V Sc = hc ? zn[pc] : zero;
+        const V Ac = (hc && !equator) ? zs[pc] : zero;
+        const T fq = (T)(q == 0 ? 1.0 : A.mfactor1), fc = (T)A.mfactor1;
+        V ynq = K::scale(K::add(Sq, Aq), fq), ysq = K::scale(K::sub(Sq, Aq), fq);
+        if (q == 0) ynq.y = ysq.y = (T)0;
+        const V ync = K::scale(K::add(Sc, Ac), fc), ysc = K::scale(K::sub(Sc, Ac), fc);
         const V wq = K::conj(A.twpost[q]);
         auto pack = [&](V y, V yc, V wv) -> V {
             return K::conj(K::add(K::add(y, K::conj(yc)),
                                   K::mul_pi(K::mul(wv, K::sub(y, K::conj(yc))))));
         };
-        zn[ph<T>(q)] = pack(ynq, ync, wq);
-        if (!equator) zs[ph<T>(q)] = pack(ysq, ysc, wq);
+        zn[pq] = pack(ynq, ync, wq);
+        if (!equator) zs[pq] = pack(ysq, ysc, wq);
         if (q != 0 && q != qc) {
             const V wc = K::conj(A.twpost[qc]);
-            zn[ph<T>(qc)] = pack(ync, ynq, wc);
-            if (!equator) zs[ph<T>(qc)] = pack(ysc, ysq, wc);
+            zn[pc] = pack(ync, ynq, wc);
+            if (!equator) zs[pc] = pack(ysc, ysq, wc);
         }
     }
     __syncthreads();
@@ -674,6 +703,7 @@ FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource&
     A.rowscale = sc.rowscale;
     A.mscale0 = sc.mscale0;
     A.mscale1 = sc.mscale1;
+    A.colmax = p->d_colmax;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
@@ -684,6 +714,10 @@ template <typename T>
 cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src,
                      const FwdScale& sc, void* work, cudaStream_t s) {
     const FwdArgs<T> A = make_fwd_args<T>(p, grid, src, sc, work);
+    if (A.colmax) {
+        const cudaError_t e = cudaMemsetAsync(A.colmax, 0, 2 * (size_t)p->F * sizeof(unsigned), s);
+        if (e) return e;
+    }
     const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
     const bool strided = src.elem_stride != 1;
 #define SHT_FWD(LV) fwd_launch<T, LV>(A, strided, g, p->fft_smem, s)
@@ -736,6 +770,11 @@ cudaError_t fwd_group_impl(sht_plan_s* const* plans, int n, const void* const* g
         src.elem_stride = 1;
         const FwdScale sc{p->d_w_over_I, 1.0, 1.0};
         G.a[q] = make_fwd_args<T>(p, grids[q], src, sc, p->d_work);
+        if (p->d_colmax) {
+            const cudaError_t e =
+                cudaMemsetAsync(p->d_colmax, 0, 2 * (size_t)p->F * sizeof(unsigned), s);
+            if (e) return e;
+        }
         G.nfg[q] = (p->F + p->G - 1) / p->G;
         G.cta_start[q + 1] = G.cta_start[q] + G.nfg[q] * p->Jh;
         if (p->fft_smem > smem) smem = p->fft_smem;
@@ -810,8 +849,9 @@ cudaError_t launch_fft_inverse_group(sht_plan_s* const* plans, int n,
 size_t fft_smem_bytes(int I, int G, bool fp64) {
     const size_t L = (size_t)I / 2;
     const size_t v = fp64 ? sizeof(double2) : sizeof(float2);
-    // padded rows + per-pass twiddle tables (fewer than L entries)
-    return (2 * (size_t)G * fft_row_pitch((int)L, fp64) + L) * v;
+    // padded rows + per-pass twiddle tables (fewer than L entries) + the
+    // column maxima of the forward kernel's output (2 words per field)
+    return (2 * (size_t)G * fft_row_pitch((int)L, fp64) + L) * v + 8 * (size_t)G;
 }
 
 cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,

@@ -33,6 +33,7 @@
 // a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
 // waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -52,10 +53,14 @@ struct SplitProb {
     int nkt;           // K tiles of TK
     int b_stride;      // floats between B rows
     int o_stride;      // floats between output rows
+    long long rs_off;  // first row of this problem in the row-scale array
 };
 
 struct SplitTables {
     int terms = 3;
+    bool fp16 = false;
+    float* rs_fwd = nullptr;      // FP16 plans: 1 / row scale of each A row
+    float* rs_inv = nullptr;
     unsigned char* fwd_planes = nullptr;   // terms planes of fwd_plane_bytes
     size_t fwd_plane_bytes = 0;
     unsigned char* inv_planes = nullptr;
@@ -87,7 +92,8 @@ template <int T> struct Cfg {
     static constexpr int BBF_OFF = RAW_OFF + RAW_BYTES;
     static constexpr int STAGE_BYTES = BBF_OFF + T * B_TILE_BYTES;
     static constexpr int BAR_OFF = NS * STAGE_BYTES;
-    static constexpr int SMEM = BAR_OFF + 256;
+    static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
+    static constexpr int SMEM = CSI_OFF + TN * 4;
 };
 
 struct GemmArgs {
@@ -100,7 +106,22 @@ struct GemmArgs {
     int C;                          // valid columns (2F)
     int raw_bulk;                   // 1: B rows arrive by bulk copy (16-byte aligned)
     int* status;
+    const float* rs_inv;            // FP16: 1 / row scale per A row (pr.rs_off + row)
+    const unsigned* colmax;         // FP16: max |B| per column (float bits)
 };
+
+// FP16 operands are scaled by powers of two into [-1, 1): column c of B by
+// 2^-(E+1) where 2^E <= max|B[., c]| < 2^(E+1), i.e. by the float whose
+// biased exponent is 253 - (E + 127); the product is scaled back by 2^(E+1).
+// Exponents are clamped so that both stay normal floats.
+__device__ __forceinline__ float col_scale(unsigned maxbits) {
+    const unsigned eb = min(maxbits >> 23, 252u);
+    return __uint_as_float((253u - eb) << 23);
+}
+__device__ __forceinline__ float col_unscale(unsigned maxbits) {
+    const unsigned eb = min(maxbits >> 23, 252u);
+    return __uint_as_float((eb + 1u) << 23);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -168,13 +189,45 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
                             ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b,
-                                         uint32_t accum) {
+// The same with FP16 A and B (format 0 in both fields).
+constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(TN >> 3) << 17) |
+                               ((uint32_t)(TM >> 4) << 24);
+
+template <bool F16>
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b,
+                                        uint32_t accum) {
+    const uint32_t idesc = F16 ? kIdescF16 : kIdesc;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// Terms of 16-bit floats.  BF16: x_1 = bf16(x), x_{t+1} = bf16(x - x_1 -
+// .. - x_t).  FP16 (x scaled into [-1, 1) first): x_1 = fp16(x), and the
+// remainder scaled by 2^11 so that it keeps FP16's precision:
+// x_2 = fp16(2^11 (x - x_1)), x_3 = fp16(2^11 (x - x_1) - x_2), so that
+// x = x_1 + 2^-11 (x_2 + x_3) + O(2^-35).
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<false>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<true>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <bool F16>
+__device__ __forceinline__ float round16(float x) {
+    if constexpr (F16)
+        return __half2float(__float2half_rn(x));
+    else
+        return __bfloat162float(__float2bfloat16_rn(x));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -195,14 +248,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
 extern __shared__ __align__(1024) unsigned char split_smem[];
 
-template <int T>
+template <int T, bool F16>
 __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 tile) {
     using CF = Cfg<T>;
     constexpr int NS = CF::NS;
@@ -296,6 +344,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                     for (int a = 0; a < T; ++a) {
 #pragma unroll
                         for (int b = 0; b < T - a; ++b) {
+                            // FP16: x_2 y_2 has weight 2^-22 (below 2^-24 of
+                            // the scaled operands) and is dropped
+                            if (F16 && a == 1 && b == 1) continue;
                             const uint64_t ad = sdesc(st + a * A_TILE_BYTES + ks * 256, 128, kSBO);
                             const uint64_t bd = sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, kSBO);
                             // (0,0) -> leading accumulator; the first of the
@@ -303,7 +354,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                             const bool lead = (a == 0 && b == 0);
                             const uint32_t acc =
                                 (it > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
-                            mma_bf16(lead ? tmem : tmem + TN, ad, bd, acc);
+                            mma_f16<F16>(lead ? tmem : tmem + TN, ad, bd, acc);
                         }
                     }
                 }
@@ -318,6 +369,16 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         // global memory (rows not 16-byte aligned: odd field counts)
         const int tid = threadIdx.x;   // 0..NCONV-1
         const int cbase = ct * TN;
+        static_assert(NCONV % TN == 0, "a converter thread keeps one column");
+        float cs = 1.f;
+        float* csi_s = reinterpret_cast<float*>(smem + CF::CSI_OFF);
+        if (F16) {
+            const int cg = cbase + tid % TN;
+            if (cg < g.C) cs = col_scale(g.colmax[cg]);
+            if (tid < TN) csi_s[tid] = cg < g.C ? col_unscale(g.colmax[cg]) : 0.f;
+            // the epilogue of all converter warps reads the table
+            asm volatile("bar.sync 1, %0;" ::"r"(NCONV) : "memory");
+        }
         for (int it = 0; it < nkt; ++it) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
@@ -348,20 +409,24 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                                   : 0.f;
                 }
                 const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
+                if (F16) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) x[e] *= cs;
+                }
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
                     float y[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(x[e]);
-                        y[e] = __bfloat162float(hb);
+                        y[e] = round16<F16>(x[e]);
                         x[e] -= y[e];
+                        if (F16 && t == 0) x[e] *= 2048.f;   // x_2, x_3 carry weight 2^-11
                     }
                     uint4 pk;
-                    pk.x = pack_bf16(y[0], y[1]);
-                    pk.y = pack_bf16(y[2], y[3]);
-                    pk.z = pack_bf16(y[4], y[5]);
-                    pk.w = pack_bf16(y[6], y[7]);
+                    pk.x = pack2<F16>(y[0], y[1]);
+                    pk.y = pack2<F16>(y[2], y[3]);
+                    pk.z = pack2<F16>(y[4], y[5]);
+                    pk.w = pack2<F16>(y[6], y[7]);
                     *reinterpret_cast<uint4*>(bst + t * B_TILE_BYTES + off) = pk;
                 }
             }
@@ -389,9 +454,21 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
                 tmem_ld16(ta, r);
                 tmem_ld16(ta + TN, r2);
+                if (F16) {
+                    // lead + 2^-11 corrections, then undo the row and column scales
+                    const float rsi = row_ok ? g.rs_inv[pr.rs_off + row] : 0.f;
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    r[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(r2[i]));
+                    for (int i = 0; i < 16; ++i) {
+                        const float csi = csi_s[ch * 16 + i];
+                        r[i] = __float_as_uint(
+                            (__uint_as_float(r[i]) + __uint_as_float(r2[i]) * (1.f / 2048.f)) *
+                            rsi * csi);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        r[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(r2[i]));
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) r[i] = 0u;
@@ -433,9 +510,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     }
 }
 
-template <int T>
+template <int T, bool F16>
 __global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(const __grid_constant__ GemmArgs g) {
-    split_gemm_body<T>(g, g.tiles[blockIdx.x]);
+    split_gemm_body<T, F16>(g, g.tiles[blockIdx.x]);
 }
 
 // Grouped launch: tile.w is the plan's index in the group.
@@ -445,11 +522,11 @@ struct GemmGroup {
     const int4* tiles;
 };
 
-template <int T>
+template <int T, bool F16>
 __global__ void __launch_bounds__(NTHREADS, 2)
     split_gemm_group_kernel(const __grid_constant__ GemmGroup G) {
     const int4 t = G.tiles[blockIdx.x];
-    split_gemm_body<T>(G.a[t.w], t);
+    split_gemm_body<T, F16>(G.a[t.w], t);
 }
 
 // Split the FP64 P~ table into T BF16 planes, pre-tiled (see top of file).
@@ -485,6 +562,107 @@ __global__ void split_table_kernel(const double* __restrict__ pnm, int ldp, int 
     }
 }
 
+// The same for FP16 terms, with one power-of-two scale per A row: row r is
+// scaled by 2^-e, where 2^(e-1) <= max_k |A[r][k]| < 2^e (e clamped to
+// [-100, 100]), so that its entries lie in [-1, 1); rs_inv[rs_off + r] = 2^e
+// undoes it in the epilogue.  One warp per row finds the row maximum.
+__global__ void split_table_f16_kernel(const double* __restrict__ pnm, int ldp, int N, int Jh,
+                                       const SplitProb* __restrict__ probs, int inverse, int T,
+                                       unsigned char* planes, long long plane_bytes,
+                                       float* rs_inv) {
+    const int p = blockIdx.x;
+    const int m = p >> 1, q = p & 1;
+    const SplitProb pr = probs[p];
+    const size_t row0 = coef_offset(N, m) + q;
+    const long long K32 = (long long)pr.nkt * TK;
+    auto aval = [&](int r, int k) -> double {
+        if (!inverse) return (r < pr.Mrows && k < Jh) ? pnm[(row0 + 2 * (size_t)r) * ldp + k] : 0.0;
+        return (r < Jh && k < pr.K) ? pnm[(row0 + 2 * (size_t)k) * ldp + r] : 0.0;
+    };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < pr.R8; r += nw) {
+        double mx = 0.0;
+        for (long long k = lane; k < K32; k += 32) mx = fmax(mx, fabs(aval(r, (int)k)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            int e = 0;
+            if (mx > 0.0) frexp(mx, &e);
+            e = max(-100, min(100, e));
+            rs_inv[pr.rs_off + r] = ldexpf(1.f, e);
+        }
+    }
+    __syncthreads();
+    const long long n_el = (long long)pr.R8 * K32;
+    for (long long e = threadIdx.x; e < n_el; e += blockDim.x) {
+        const int r = (int)(e / K32);
+        const int k = (int)(e % K32);
+        double v = aval(r, k) / (double)rs_inv[pr.rs_off + r];   // exact: a power of two
+        const int kt = k / TK, kk = k % TK;
+        const long long off = pr.a_off + (long long)kt * pr.R8 * TK * 2 +
+                              (long long)(((r >> 3) * (TK / 8) + (kk >> 3)) * 128 +
+                                          (r & 7) * 16 + (kk & 7) * 2);
+        for (int t = 0; t < T; ++t) {
+            const __half h = __double2half(v);
+            *reinterpret_cast<__half*>(planes + t * plane_bytes + off) = h;
+            v -= (double)__half2float(h);
+            if (t == 0) v *= 2048.0;
+        }
+    }
+}
+
+// Column maxima of a row-major FP32 operand of nrows x C (the spectrum of
+// an inverse GEMM); the imaginary column of each field is skipped in the
+// first skip_odd rows (the m = 0 coefficients, whose imaginary parts are
+// not inputs).  Block (x, y) covers columns 32x .. 32x+31 of a contiguous
+// range of rows; its 8 warps stride that range with 8 independent loads in
+// flight per thread, then reduce through shared memory to one atomic per
+// column.  colmax must be zero on entry.
+__global__ void __launch_bounds__(256) colmax_kernel(const float* __restrict__ B,
+                                                     long long nrows, int C, int skip_odd,
+                                                     unsigned* colmax) {
+    __shared__ float red[8][32];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const long long per = (nrows + gridDim.y - 1) / gridDim.y;
+    const long long r0 = (long long)blockIdx.y * per;
+    const long long r1 = min(nrows, r0 + per);
+    float mx = 0.f;
+    if (c < C) {
+        const long long rs = ((c & 1) ? max(r0, (long long)skip_odd) : r0) + threadIdx.y;
+        long long r = rs;
+        for (; r + 56 < r1; r += 64) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldg(B + (r + 8 * u) * C + c);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = fmaxf(mx, fabsf(v[u]));
+        }
+        for (; r < r1; r += 8) mx = fmaxf(mx, fabsf(__ldg(B + r * C + c)));
+    }
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < C) {
+#pragma unroll
+        for (int y = 1; y < 8; ++y) mx = fmaxf(mx, red[y][threadIdx.x]);
+        atomicMax(&colmax[c], __float_as_uint(mx));
+    }
+}
+
+cudaError_t launch_colmax_inverse(const sht_plan_s* p, const void* spec, cudaStream_t s) {
+    const int C = 2 * p->F;
+    unsigned* cm = p->d_colmax + C;
+    cudaError_t e = cudaMemsetAsync(cm, 0, (size_t)C * sizeof(unsigned), s);
+    if (e) return e;
+    const long long nrows = (long long)p->ncoef;
+    const int cx = (C + 31) / 32;
+    // about 16 blocks per SM in all, each over at least 64 rows
+    long long ry = std::max<long long>(1, (16LL * p->num_sms + cx - 1) / cx);
+    ry = std::min<long long>(ry, std::max<long long>(1, nrows / 64));
+    colmax_kernel<<<dim3(cx, (unsigned)ry), dim3(32, 8), 0, s>>>(
+        static_cast<const float*>(spec), nrows, C, p->N + 1, cm);
+    return cudaGetLastError();
+}
+
 int terms_of(int prec) { return (prec == SHT_BF16X2 || prec == SHT_FP16X2) ? 2 : 3; }
 
 // Problems (one per (m, parity)) and tiles of both directions for
@@ -498,6 +676,7 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
     tf.clear();
     ti.clear();
     fwd_bytes = inv_bytes = 0;
+    long long fwd_rows = 0, inv_rows = 0;
     const int nct = (C + TN - 1) / TN;
     for (int m = 0; m <= N; ++m) {
         for (int q = 0; q < 2; ++q) {
@@ -515,6 +694,8 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             f.o_off = row0 * C;
             f.o_stride = 2 * C;
             fwd_bytes += (long long)f.R8 * f.nkt * TK * 2;
+            f.rs_off = fwd_rows;
+            fwd_rows += f.R8;
             for (int mt = 0; mt * TM < R; ++mt)
                 for (int c = 0; c < nct; ++c) tf.push_back(make_int4(2 * m + q, mt, c, plan));
             SplitProb& v = pi[2 * m + q];
@@ -528,6 +709,8 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             v.o_off = (long long)(2 * m + q) * Jh * C;
             v.o_stride = C;
             inv_bytes += (long long)v.R8 * v.nkt * TK * 2;
+            v.rs_off = inv_rows;
+            inv_rows += v.R8;
             for (int mt = 0; mt * TM < Jh; ++mt)
                 for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, plan));
         }
@@ -547,7 +730,17 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     // rows of B are 16-byte aligned when C is a multiple of 4 floats
     g.raw_bulk = ((g.C & 3) == 0) && (((uintptr_t)B & 15) == 0) ? 1 : 0;
     g.status = p->d_status;
+    g.rs_inv = inverse ? st->rs_inv : st->rs_fwd;
+    g.colmax = p->d_colmax ? p->d_colmax + (inverse ? g.C : 0) : nullptr;
     return g;
+}
+
+template <int T, bool F16>
+cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
+    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16>, Cfg<T>::SMEM);
+    if (e) return e;
+    split_gemm_kernel<T, F16><<<ntiles, NTHREADS, Cfg<T>::SMEM, s>>>(g);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* O,
@@ -556,28 +749,27 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
     const GemmArgs g = make_gemm_args(p, inverse, B, O);
     const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
     if (ntiles == 0) return cudaSuccess;
-    cudaError_t e;
-    if (st->terms == 3) {
-        if ((e = ensure_smem((const void*)split_gemm_kernel<3>, Cfg<3>::SMEM))) return e;
-        split_gemm_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(g);
-    } else {
-        if ((e = ensure_smem((const void*)split_gemm_kernel<2>, Cfg<2>::SMEM))) return e;
-        split_gemm_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(g);
+    if (st->fp16) {
+        // forward: the FFT kernel gathered the column maxima of its output
+        if (inverse) {
+            const cudaError_t e = launch_colmax_inverse(p, B, s);
+            if (e) return e;
+        }
+        return st->terms == 3 ? gemm_launch<3, true>(g, ntiles, s)
+                              : gemm_launch<2, true>(g, ntiles, s);
     }
-    return cudaGetLastError();
+    return st->terms == 3 ? gemm_launch<3, false>(g, ntiles, s)
+                          : gemm_launch<2, false>(g, ntiles, s);
 }
 
 }  // namespace
 
 cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
-    if (p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3) {
-        set_error("FP16 split plans are not available in this build (BF16 only)");
-        return cudaErrorNotSupported;
-    }
     SplitTables* st = new (std::nothrow) SplitTables();
     if (!st) return cudaErrorMemoryAllocation;
     p->split = st;
     st->terms = terms_of(p->prec);
+    st->fp16 = p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3;
     const int N = p->N, Jh = p->Jh, C = 2 * p->F;
     const int nprob = 2 * (N + 1);
     std::vector<SplitProb> pf, pi;
@@ -598,6 +790,16 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
         set_error("split tables: %s", cudaGetErrorString(e));
         return e;
     }
+    if (st->fp16) {
+        const size_t rf = (size_t)(pf.back().rs_off + pf.back().R8);
+        const size_t ri = (size_t)(pi.back().rs_off + pi.back().R8);
+        if ((e = cudaMalloc(&st->rs_fwd, (rf + 1) * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&st->rs_inv, (ri + 1) * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_colmax, 2 * (size_t)C * sizeof(unsigned))) != cudaSuccess) {
+            set_error("split scales: %s", cudaGetErrorString(e));
+            return e;
+        }
+    }
     // rows of A beyond R8 inside a 128-row tile are never copied; zero the
     // planes so K padding and row padding read as zero
     if ((e = cudaMemsetAsync(st->fwd_planes, 0, st->fwd_plane_bytes * st->terms, s)) ||
@@ -611,12 +813,21 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
         (e = cudaMemcpyAsync(st->d_tiles_inv, ti.data(), ti.size() * sizeof(int4),
                              cudaMemcpyHostToDevice, s)))
         return e;
-    split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_fwd, 0,
-                                            st->terms, st->fwd_planes,
-                                            (long long)st->fwd_plane_bytes);
-    split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_inv, 1,
-                                            st->terms, st->inv_planes,
-                                            (long long)st->inv_plane_bytes);
+    if (st->fp16) {
+        split_table_f16_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_fwd, 0,
+                                                    st->terms, st->fwd_planes,
+                                                    (long long)st->fwd_plane_bytes, st->rs_fwd);
+        split_table_f16_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_inv, 1,
+                                                    st->terms, st->inv_planes,
+                                                    (long long)st->inv_plane_bytes, st->rs_inv);
+    } else {
+        split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_fwd, 0,
+                                                st->terms, st->fwd_planes,
+                                                (long long)st->fwd_plane_bytes);
+        split_table_kernel<<<nprob, 256, 0, s>>>(p->d_pnm, p->ldp, N, Jh, st->d_probs_inv, 1,
+                                                st->terms, st->inv_planes,
+                                                (long long)st->inv_plane_bytes);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaStreamSynchronize(s);   // host vectors above must outlive the copies
 }
@@ -625,11 +836,12 @@ void split_tables_destroy(sht_plan_s* p) {
     SplitTables* st = p->split;
     if (!st) return;
     void* ptrs[] = {st->fwd_planes, st->inv_planes, st->d_probs_fwd, st->d_probs_inv,
-                    st->d_tiles_fwd, st->d_tiles_inv};
+                    st->d_tiles_fwd, st->d_tiles_inv, st->rs_fwd, st->rs_inv, p->d_colmax};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete st;
     p->split = nullptr;
+    p->d_colmax = nullptr;
 }
 
 // Tiles of a group of split plans (same term count), heaviest first: every
@@ -653,6 +865,14 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
     for (auto& e : all) out.push_back(e.second);
 }
 
+template <int T, bool F16>
+cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
+    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16>, Cfg<T>::SMEM);
+    if (e) return e;
+    split_gemm_group_kernel<T, F16><<<ntiles, NTHREADS, Cfg<T>::SMEM, s>>>(G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
                                const void* const* in, void* const* out, const int4* tiles,
                                int ntiles, cudaStream_t s) {
@@ -661,15 +881,19 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
     G.n = n;
     G.tiles = tiles;
     for (int q = 0; q < n; ++q) G.a[q] = make_gemm_args(plans[q], inverse, in[q], out[q]);
-    cudaError_t e;
-    if (plans[0]->split->terms == 3) {
-        if ((e = ensure_smem((const void*)split_gemm_group_kernel<3>, Cfg<3>::SMEM))) return e;
-        split_gemm_group_kernel<3><<<ntiles, NTHREADS, Cfg<3>::SMEM, s>>>(G);
-    } else {
-        if ((e = ensure_smem((const void*)split_gemm_group_kernel<2>, Cfg<2>::SMEM))) return e;
-        split_gemm_group_kernel<2><<<ntiles, NTHREADS, Cfg<2>::SMEM, s>>>(G);
+    const SplitTables* st = plans[0]->split;
+    if (st->fp16 && inverse)
+        for (int q = 0; q < n; ++q) {
+            const cudaError_t e = launch_colmax_inverse(plans[q], in[q], s);
+            if (e) return e;
+        }
+    const int key = st->terms * 2 + (st->fp16 ? 1 : 0);
+    switch (key) {
+        case 7: return group_launch<3, true>(G, ntiles, s);
+        case 5: return group_launch<2, true>(G, ntiles, s);
+        case 6: return group_launch<3, false>(G, ntiles, s);
+        default: return group_launch<2, false>(G, ntiles, s);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_legendre_fwd_split(const sht_plan_s* p, const void* work, void* spec,

@@ -9,6 +9,14 @@ Tolerances (relative L2 over the whole output, per direction):
                    the tensor cores accumulate each K=16 block in FP32, so
                    about sqrt(K/16) * 2^-24 ~ 4e-7 is expected at K = 641.
   bf16x2: 5e-5  -- two BF16 terms carry 16 bits: ~2^-16 = 1.5e-5 per operand.
+  fp16x2, fp16x3: operands scaled by powers of two into [-1, 1) (per P~ row,
+                  per real column), x = x_1 + 2^-11 (x_2 [+ x_3]).  Per
+                  product the error is at most 2^-24 (x2: representation of
+                  each operand) x 2 + 2^-24 (the dropped x_2 y_2) of
+                  rowmax * colmax, i.e. 1.8e-7; fp16x3 removes the first
+                  two.  Relative to the output this is multiplied by the
+                  ratio of the column maximum to the typical entry (up to
+                  ~5 for these spectra), so: fp16x2 2e-6, fp16x3 1e-6.
 """
 import json
 import os
@@ -23,7 +31,8 @@ from sht_testutil import built_lib, rel_l2, to_cuda
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 1e-6, "bf16x2": 5e-5}
+TOL = {"bf16x3": 1e-6, "bf16x2": 5e-5, "fp16x3": 1e-6, "fp16x2": 2e-6}
+PRECS = ["bf16x3", "bf16x2", "fp16x3", "fp16x2"]
 
 CASES = [
     (31, 65, 128, 1),
@@ -51,7 +60,7 @@ def _c64(a):
     return np.asarray(a).astype(np.complex64).astype(np.complex128)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2"])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,J,I,F", CASES)
 def test_split_forward_inverse_match_oracle(sht, prec, N, J, I, F):
     p = sht.Plan(N, J, I, F, prec)
@@ -67,9 +76,10 @@ def test_split_forward_inverse_match_oracle(sht, prec, N, J, I, F):
     p.status()
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
 @pytest.mark.parametrize("N,J,I,F", [(31, 65, 128, 3), (63, 129, 256, 4)])
-def test_split_adjoints_and_restriction(sht, N, J, I, F):
-    p = sht.Plan(N, J, I, F, "bf16x3")
+def test_split_adjoints_and_restriction(sht, prec, N, J, I, F):
+    p = sht.Plan(N, J, I, F, prec)
     a = _c64(W.random_spectrum(N, F, "n^-1.5", seed=900 + N))
     x = _f32(W.random_grid(F, J, I, seed=901 + N))
     g0 = p.adjoint(0, to_cuda(a, torch.complex64)).cpu().numpy()
@@ -83,8 +93,8 @@ def test_split_adjoints_and_restriction(sht, N, J, I, F):
 
 
 def test_split_t319_errors_per_field(sht):
-    """T319 x 300 field-levels: per-field spectral and grid errors of both
-    BF16 splits against the oracle on sampled fields (all fields run on the
+    """T319 x 300 field-levels: per-field spectral and grid errors of the
+    four splits against the oracle on sampled fields (all fields run on the
     GPU).  Writes the table to $SHT_REPORT_DIR if set."""
     w = W.WORKLOADS["T319"]
     fields = [0, 1, 99, 150, 299]
@@ -94,7 +104,7 @@ def test_split_t319_errors_per_field(sht):
     ref_s = O.analysis(x[fields], w.N)
     ref_g = O.synthesis(a[:, fields], w.N, w.J, w.I)
     report = {}
-    for prec in ("bf16x3", "bf16x2"):
+    for prec in PRECS:
         p = sht.Plan(w.N, w.J, w.I, w.F, prec)
         s = p.forward(to_cuda(x, torch.float32)).cpu().numpy()[:, fields]
         g = p.inverse(to_cuda(a, torch.complex64)).cpu().numpy()[fields]
@@ -110,9 +120,10 @@ def test_split_t319_errors_per_field(sht):
             json.dump(report, fh, indent=1)
 
 
-def test_split_t639_sampled(sht):
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x2"])
+def test_split_t639_sampled(sht, prec):
     w = W.WORKLOADS["T639"]
-    p = sht.Plan(w.N, w.J, w.I, w.F, "bf16x3")
+    p = sht.Plan(w.N, w.J, w.I, w.F, prec)
     fields = [0, 77, 255]
     ms = [0, 1, 2, 320, 638, 639]
     x = _f32(np.stack([W.random_grid_field(f, w.J, w.I) for f in range(w.F)]))
@@ -124,10 +135,43 @@ def test_split_t639_sampled(sht):
         d = got[r0:r0 + w.N - m + 1][:, fields] - ref[m]
         num += np.sum(np.abs(d) ** 2)
         den += np.sum(np.abs(ref[m]) ** 2)
-    assert np.sqrt(num / den) <= 1e-6, np.sqrt(num / den)
+    assert np.sqrt(num / den) <= TOL[prec], np.sqrt(num / den)
     a = _c64(W.workload_spectrum(w))
     grid = p.inverse(to_cuda(a, torch.complex64)).cpu().numpy()
     rows = [1, 2, 640, 641, 1281]
     gref = O.synthesis_rows(a[:, fields], w.N, w.J, w.I, rows)
-    assert rel_l2(grid[fields][:, np.array(rows) - 1, :], gref) <= 1e-6
+    assert rel_l2(grid[fields][:, np.array(rows) - 1, :], gref) <= TOL[prec]
+    p.status()
+
+
+@pytest.mark.parametrize("prec", ["fp16x2", "fp16x3"])
+def test_fp16_scaling_range(sht, prec):
+    """FP16 splits scale each column into FP16's range: fields of magnitude
+    1e12 and 1e-12 (far outside it) keep the same relative error, an
+    all-zero field gives exactly zero, and an arbitrary Im(X_n^0) (not an
+    input) does not disturb the scale of its column."""
+    N, J, I, F = 63, 129, 256, 5
+    p = sht.Plan(N, J, I, F, prec)
+    x = W.random_grid(F, J, I, seed=1201)
+    x[1] *= 1e12
+    x[2] *= 1e-12
+    x[3] = 0.0
+    x = _f32(x)
+    got = p.forward(to_cuda(x, torch.float32)).cpu().numpy()
+    ref = O.analysis(x, N)
+    for f in (0, 1, 2, 4):
+        assert rel_l2(got[:, f], ref[:, f]) <= TOL[prec], (f, rel_l2(got[:, f], ref[:, f]))
+    assert np.all(got[:, 3] == 0)
+    a = W.random_spectrum(N, F, "n^-1.5", seed=1202)
+    a[:, 1] *= 1e12
+    a[:, 2] *= 1e-12
+    a[:, 3] = 0.0
+    a = _c64(a)
+    ref_g = O.synthesis(a, N, J, I)
+    a_junk = a.copy()
+    a_junk[:N + 1] += 1j * 1e30            # Im(X_n^0): ignored on input
+    g = p.inverse(to_cuda(a_junk, torch.complex64)).cpu().numpy()
+    for f in (0, 1, 2, 4):
+        assert rel_l2(g[f], ref_g[f]) <= TOL[prec], (f, rel_l2(g[f], ref_g[f]))
+    assert np.all(g[3] == 0)
     p.status()
