@@ -259,6 +259,35 @@ __device__ __forceinline__ void bfly(typename Vec2<T>::type* z, int base, int M,
     for (int k1 = 0; k1 < R; ++k1) z[ph<T>(base + k1 * M)] = a[Dft<T, R>::pos(k1)];
 }
 
+// The same with the span M a compile-time constant.  When M is a multiple
+// of the padding period P (pad one element per P), or R M divides P, the
+// padded positions of the R elements are ph(base) + t STEP with a constant
+// STEP, so one padded index serves the whole butterfly.
+template <typename T, int R, int M>
+__device__ __forceinline__ void bfly_fixed(typename Vec2<T>::type* z, int base,
+                                           const typename Vec2<T>::type* tw, int n1) {
+    using V = typename Vec2<T>::type;
+    using K = C2<T>;
+    constexpr int P = 1 << PadShift<T>::value;
+    if constexpr (M % P == 0 || P % (R * M) == 0) {
+        constexpr int STEP = (M % P == 0) ? M + M / P : M;
+        V* zb = z + ph<T>(base);
+        V a[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) a[t] = zb[t * STEP];
+        Dft<T, R>::run(a);
+        if (M > 1 && n1 != 0) {
+#pragma unroll
+            for (int k1 = 1; k1 < R; ++k1)
+                a[Dft<T, R>::pos(k1)] = K::mul(a[Dft<T, R>::pos(k1)], tw[(k1 - 1) * M + n1]);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) zb[k1 * STEP] = a[Dft<T, R>::pos(k1)];
+    } else {
+        bfly<T, R>(z, base, M, tw, n1);
+    }
+}
+
 // In-place mixed-radix DIF FFT over `nrows` padded rows (pitch LP), shape
 // known at run time.
 template <typename T>
@@ -321,7 +350,7 @@ __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int n
             const int b = idx - row * NB;
             const int blk = b / M;
             const int n1 = b - blk * M;
-            bfly<T, R>(rows + (size_t)row * LP, blk * S + n1, M, twp + OFF, n1);
+            bfly_fixed<T, R, M>(rows + (size_t)row * LP, blk * S + n1, twp + OFF, n1);
         }
         __syncthreads();
         passes_fixed<T, L, P + 1>(rows, nrows, LP, twp);
@@ -478,42 +507,68 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             atomicMax(&smax[2 * mcur + 1], __float_as_uint(mim));
         }
     };
-    for (Walk2 w(tid, nf); w.major * nf + w.minor < nout; w.next()) {
-        const int m = w.major;
-        const int fl = w.minor;
-        const int pm = ph<T>(rev_of<T, LT>(m, A.rev));
-        const int pc = ph<T>(rev_of<T, LT>(m == 0 ? 0 : L - m, A.rev));
-        const V wt = A.twpost[m];
-        auto real_spec = [&](const V* z) -> V {
-            const V zm = z[pm];
-            const V zc = K::conj(z[pc]);
-            const V e = K::add(zm, zc);                  // 2 E_m
-            const V o = K::mul_mi(K::sub(zm, zc));       // 2 O_m
-            return K::add(e, K::mul(wt, o));             // 2 X_m
-        };
-        const V xn = real_spec(rows + (size_t)fl * LP);
-        V S, Asym;
-        if (equator) {
-            S = xn;
-            Asym = K::make((T)0, (T)0);
-        } else {
-            const V xs = real_spec(rows + (size_t)(nf + fl) * LP);
-            S = K::add(xn, xs);
-            Asym = K::sub(xn, xs);
+    auto record = [&](int fl, V os, V oa) {
+        if (fl != mcur) {
+            flush();
+            mcur = fl;
+            mre = mim = 0.f;
         }
-        const T sc = (T)0.5 * rs * (T)(m == 0 ? A.mscale0 : A.mscale1);
-        const size_t base = ((size_t)m * 2 * A.Jh + jh) * A.F + f0 + fl;
-        const V os = K::scale(S, sc), oa = K::scale(Asym, sc);
-        A.work[base] = os;
-        A.work[base + (size_t)A.Jh * A.F] = oa;
-        if (track) {
-            if (fl != mcur) {
-                flush();
-                mcur = fl;
-                mre = mim = 0.f;
-            }
-            mre = fmaxf(mre, fmaxf(fabsf((float)os.x), fabsf((float)oa.x)));
-            mim = fmaxf(mim, fmaxf(fabsf((float)os.y), fabsf((float)oa.y)));
+        mre = fmaxf(mre, fmaxf(fabsf((float)os.x), fabsf((float)oa.x)));
+        mim = fmaxf(mim, fmaxf(fabsf((float)os.y), fabsf((float)oa.y)));
+    };
+    // 2 X_m = (Z_m + conj Z_{L-m}) + W_I^m (-i)(Z_m - conj Z_{L-m})
+    auto real_spec = [&](V zm, V zc, V wt) -> V {
+        const V c = K::conj(zc);
+        return K::add(K::add(zm, c), K::mul(wt, K::mul_mi(K::sub(zm, c))));
+    };
+    // output scales, converted once (FP64 conversions use the narrow FP64 pipe)
+    const T sc0 = (T)0.5 * rs * (T)A.mscale0, sc1 = (T)0.5 * rs * (T)A.mscale1;
+    // two outputs (m, fl) per iteration, idx and idx + NT, with all shared-
+    // memory reads of both issued before any arithmetic
+    Walk2 wa(tid, nf), wb(tid + NT, nf);
+    for (; wa.major * nf + wa.minor < nout; wa.next(), wa.next(), wb.next(), wb.next()) {
+        const bool hb = wb.major * nf + wb.minor < nout;
+        const int ma = wa.major, fa = wa.minor;
+        const int mb = hb ? wb.major : ma, fb = hb ? wb.minor : fa;
+        const int pma = ph<T>(rev_of<T, LT>(ma, A.rev));
+        const int pca = ph<T>(rev_of<T, LT>(ma == 0 ? 0 : L - ma, A.rev));
+        const int pmb = ph<T>(rev_of<T, LT>(mb, A.rev));
+        const int pcb = ph<T>(rev_of<T, LT>(mb == 0 ? 0 : L - mb, A.rev));
+        const V* na = rows + (size_t)fa * LP;
+        const V* nb = rows + (size_t)fb * LP;
+        const V a_nm = na[pma], a_nc = na[pca], b_nm = nb[pmb], b_nc = nb[pcb];
+        V a_sm = K::make((T)0, (T)0), a_sc = a_sm, b_sm = a_sm, b_sc = a_sm;
+        if (!equator) {
+            const V* sa = na + (size_t)nf * LP;
+            const V* sb = nb + (size_t)nf * LP;
+            a_sm = sa[pma];
+            a_sc = sa[pca];
+            b_sm = sb[pmb];
+            b_sc = sb[pcb];
+        }
+        const V wta = A.twpost[ma], wtb = A.twpost[mb];
+        const T sca = ma == 0 ? sc0 : sc1;
+        const T scb = mb == 0 ? sc0 : sc1;
+        const V xan = real_spec(a_nm, a_nc, wta), xbn = real_spec(b_nm, b_nc, wtb);
+        V Sa = xan, Aa = K::make((T)0, (T)0), Sb = xbn, Ab = Aa;
+        if (!equator) {
+            const V xas = real_spec(a_sm, a_sc, wta), xbs = real_spec(b_sm, b_sc, wtb);
+            Sa = K::add(xan, xas);
+            Aa = K::sub(xan, xas);
+            Sb = K::add(xbn, xbs);
+            Ab = K::sub(xbn, xbs);
+        }
+        const V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
+        const size_t basea = ((size_t)ma * 2 * A.Jh + jh) * A.F + f0 + fa;
+        A.work[basea] = osa;
+        A.work[basea + (size_t)A.Jh * A.F] = oaa;
+        if (track) record(fa, osa, oaa);
+        if (hb) {
+            const V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
+            const size_t baseb = ((size_t)mb * 2 * A.Jh + jh) * A.F + f0 + fb;
+            A.work[baseb] = osb;
+            A.work[baseb + (size_t)A.Jh * A.F] = oab;
+            if (track) record(fb, osb, oab);
         }
     }
     if (track) {
@@ -558,42 +613,45 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     }
     cp_async_wait_all();
     __syncthreads();
-    // One thread owns frequencies (q, L-q) of field fl in both hemispheres:
+    // One thread owns frequencies (q, L-q) of all fields in both hemispheres
     // Y_m = fac (S_m +- A_m) (Y_0 real, Y_m = 0 for m > N; stale slots beyond
     // N are never read), then the Hermitian packing
     //   Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q}),
     // stored as conj(Z) in place.
     const int half = L / 2;
     const int N = A.N;
-    for (Walk2 w(tid, half + 1); w.major < nf; w.next()) {
-        const int fl = w.major, q = w.minor;
+    const T mf1 = (T)A.mfactor1;
+    auto pack = [&](V y, V yc, V wv) -> V {
+        return K::conj(K::add(K::add(y, K::conj(yc)),
+                              K::mul_pi(K::mul(wv, K::sub(y, K::conj(yc))))));
+    };
+    for (int q = tid; q <= half; q += NT) {
         const int qc = L - q;   // >= q, as q <= L/2
-        V* zn = rows + (size_t)fl * LP;
-        V* zs = rows + (size_t)(nf + fl) * LP;
-        const V zero = K::make((T)0, (T)0);
         const int pq = ph<T>(q), pc = ph<T>(qc);
-        // S and A at frequencies q and L - q, each read once (zero above N;
-        // Y_L = 0 for q = 0)
         const bool hq = q <= N, hc = q != 0 && qc <= N;
-        const V Sq = hq ? zn[pq] : zero;
-        const V Aq = (hq && !equator) ? zs[pq] : zero;
-        const V Sc = hc ? zn[pc] : zero;
-        const V Ac = (hc && !equator) ? zs[pc] : zero;
-        const T fq = (T)(q == 0 ? 1.0 : A.mfactor1), fc = (T)A.mfactor1;
-        V ynq = K::scale(K::add(Sq, Aq), fq), ysq = K::scale(K::sub(Sq, Aq), fq);
-        if (q == 0) ynq.y = ysq.y = (T)0;
-        const V ync = K::scale(K::add(Sc, Ac), fc), ysc = K::scale(K::sub(Sc, Ac), fc);
+        const bool pair = q != 0 && q != qc;
+        const T fq = q == 0 ? (T)1 : mf1, fc = mf1;
         const V wq = K::conj(A.twpost[q]);
-        auto pack = [&](V y, V yc, V wv) -> V {
-            return K::conj(K::add(K::add(y, K::conj(yc)),
-                                  K::mul_pi(K::mul(wv, K::sub(y, K::conj(yc))))));
-        };
-        zn[pq] = pack(ynq, ync, wq);
-        if (!equator) zs[pq] = pack(ysq, ysc, wq);
-        if (q != 0 && q != qc) {
-            const V wc = K::conj(A.twpost[qc]);
-            zn[pc] = pack(ync, ynq, wc);
-            if (!equator) zs[pc] = pack(ysc, ysq, wc);
+        const V wc = pair ? K::conj(A.twpost[qc]) : wq;
+        const V zero = K::make((T)0, (T)0);
+        for (int fl = 0; fl < nf; ++fl) {
+            V* zn = rows + (size_t)fl * LP;
+            V* zs = rows + (size_t)(nf + fl) * LP;
+            // S and A at frequencies q and L - q, each read once (zero above
+            // N; Y_L = 0 for q = 0)
+            const V Sq = hq ? zn[pq] : zero;
+            const V Aq = (hq && !equator) ? zs[pq] : zero;
+            const V Sc = hc ? zn[pc] : zero;
+            const V Ac = (hc && !equator) ? zs[pc] : zero;
+            V ynq = K::scale(K::add(Sq, Aq), fq), ysq = K::scale(K::sub(Sq, Aq), fq);
+            if (q == 0) ynq.y = ysq.y = (T)0;
+            const V ync = K::scale(K::add(Sc, Ac), fc), ysc = K::scale(K::sub(Sc, Ac), fc);
+            zn[pq] = pack(ynq, ync, wq);
+            if (!equator) zs[pq] = pack(ysq, ysc, wq);
+            if (pair) {
+                zn[pc] = pack(ync, ynq, wc);
+                if (!equator) zs[pc] = pack(ysc, ysq, wc);
+            }
         }
     }
     __syncthreads();
@@ -605,9 +663,25 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
         V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I);
         const V* z = rows + (size_t)r * LP;
-        for (int k = tid; k < L; k += NT) {
-            const V v = z[ph<T>(rev_of<T, LT>(k, A.rev))];
-            xv[k] = K::make(v.x * rs, -v.y * rs);
+        if constexpr (LT > 0) {
+            // all of the thread's shared-memory reads of the row first
+            constexpr int NIT = (LT + NT - 1) / NT;
+            V v[NIT];
+#pragma unroll
+            for (int i = 0; i < NIT; ++i) {
+                const int k = tid + i * NT;
+                if (LT % NT == 0 || k < LT) v[i] = z[ph<T>(rev_fixed<T, LT>(k))];
+            }
+#pragma unroll
+            for (int i = 0; i < NIT; ++i) {
+                const int k = tid + i * NT;
+                if (LT % NT == 0 || k < LT) xv[k] = K::make(v[i].x * rs, -v[i].y * rs);
+            }
+        } else {
+            for (int k = tid; k < L; k += NT) {
+                const V v = z[ph<T>(rev_of<T, LT>(k, A.rev))];
+                xv[k] = K::make(v.x * rs, -v.y * rs);
+            }
         }
     }
 }
