@@ -42,16 +42,55 @@ namespace {
 
 constexpr int NT = 256;   // threads per FFT CTA (two CTAs per SM for FP32)
 
+// Paired FP32 arithmetic (add/sub/mul.f32x2): one instruction on both
+// components of a complex value.
+__device__ __forceinline__ float2 add_f32x2(float2 a, float2 b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t*>(&a)), "l"(*reinterpret_cast<const uint64_t*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+__device__ __forceinline__ float2 sub_f32x2(float2 a, float2 b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t*>(&a)), "l"(*reinterpret_cast<const uint64_t*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+__device__ __forceinline__ float2 mul_f32x2(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t*>(&a)), "l"(*reinterpret_cast<const uint64_t*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+
 template <typename T> struct C2 {
     using V = typename Vec2<T>::type;
     static __device__ __forceinline__ V make(T x, T y) { V v; v.x = x; v.y = y; return v; }
-    static __device__ __forceinline__ V add(V a, V b) { return make(a.x + b.x, a.y + b.y); }
-    static __device__ __forceinline__ V sub(V a, V b) { return make(a.x - b.x, a.y - b.y); }
+    static __device__ __forceinline__ V add(V a, V b) {
+        if constexpr (sizeof(T) == 4)
+            return add_f32x2(a, b);
+        else
+            return make(a.x + b.x, a.y + b.y);
+    }
+    static __device__ __forceinline__ V sub(V a, V b) {
+        if constexpr (sizeof(T) == 4)
+            return sub_f32x2(a, b);
+        else
+            return make(a.x - b.x, a.y - b.y);
+    }
     static __device__ __forceinline__ V mul(V a, V b) {
         return make(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
     }
     static __device__ __forceinline__ V conj(V a) { return make(a.x, -a.y); }
-    static __device__ __forceinline__ V scale(V a, T s) { return make(a.x * s, a.y * s); }
+    static __device__ __forceinline__ V scale(V a, T s) {
+        if constexpr (sizeof(T) == 4)
+            return mul_f32x2(a, make(s, s));
+        else
+            return make(a.x * s, a.y * s);
+    }
     // multiply by -i
     static __device__ __forceinline__ V mul_mi(V a) { return make(a.y, -a.x); }
     // multiply by +i
