@@ -54,6 +54,7 @@ struct SplitProb {
     int b_stride;      // floats between B rows
     int o_stride;      // floats between output rows
     long long rs_off;  // first row of this problem in the row-scale array
+    long long bt_off;  // pre-split B: byte offset of this problem's tiles in each plane
 };
 
 struct SplitTables {
@@ -65,6 +66,9 @@ struct SplitTables {
     size_t fwd_plane_bytes = 0;
     unsigned char* inv_planes = nullptr;
     size_t inv_plane_bytes = 0;
+    unsigned char* inv_bplanes = nullptr;   // the spectrum split per call (inverse B)
+    size_t inv_bplane_bytes = 0;
+    int inv_max_nkt = 0;
     SplitProb* d_probs_fwd = nullptr;
     SplitProb* d_probs_inv = nullptr;
     int4* d_tiles_fwd = nullptr;
@@ -85,11 +89,14 @@ constexpr uint32_t kSBO = (TK / 8) * 128;   // stride between 8-row core groups
 constexpr int TMEM_COLS = 2 * TN;     // two 128 x TN FP32 accumulators
 constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
 
-// Stage layout: T A tiles | FP32 staging of B | T BF16 B tiles.
-template <int T> struct Cfg {
-    static constexpr int NS = T == 3 ? 3 : 4;   // <= 113 KB: two CTAs per SM
+// Stage layout: T A tiles | FP32 staging of B | T 16-bit B tiles.  With B
+// split beforehand (BPRE) a stage is T A tiles | T B tiles, both copied in
+// by the bulk-copy warp, and the pipeline is deeper.
+template <int T, bool BPRE = false> struct Cfg {
+    // <= 113 KB: two CTAs per SM
+    static constexpr int NS = BPRE ? (T == 3 ? 4 : 6) : (T == 3 ? 3 : 4);
     static constexpr int RAW_OFF = T * A_TILE_BYTES;
-    static constexpr int BBF_OFF = RAW_OFF + RAW_BYTES;
+    static constexpr int BBF_OFF = RAW_OFF + (BPRE ? 0 : RAW_BYTES);
     static constexpr int STAGE_BYTES = BBF_OFF + T * B_TILE_BYTES;
     static constexpr int BAR_OFF = NS * STAGE_BYTES;
     static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
@@ -108,6 +115,9 @@ struct GemmArgs {
     int* status;
     const float* rs_inv;            // FP16: 1 / row scale per A row (pr.rs_off + row)
     const unsigned* colmax;         // FP16: max |B| per column (float bits)
+    const unsigned char* bplanes;   // pre-split B: term t plane at bplanes + t * bplane_bytes
+    long long bplane_bytes;
+    int nct;                        // column tiles (pre-split B tile index = it * nct + ct)
 };
 
 // FP16 operands are scaled by powers of two into [-1, 1): column c of B by
@@ -250,9 +260,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 extern __shared__ __align__(1024) unsigned char split_smem[];
 
-template <int T, bool F16>
+template <int T, bool F16, bool BPRE>
 __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 tile) {
-    using CF = Cfg<T>;
+    using CF = Cfg<T, BPRE>;
     constexpr int NS = CF::NS;
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
@@ -308,19 +318,28 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             const int k0 = it * TK;
-            const int krows = g.raw_bulk ? max(0, min(TK, pr.K - k0)) : 0;
+            const int krows = (!BPRE && g.raw_bulk) ? max(0, min(TK, pr.K - k0)) : 0;
             unsigned char* st = smem + s * CF::STAGE_BYTES;
             if (lane == 0) {
-                mbar_expect_tx(full_a(s), abytes * T + rbytes * (uint32_t)krows);
+                mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES)
+                                                             : rbytes * (uint32_t)krows));
                 const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
                                           (long long)mt * TM * TK * 2;
                 for (int t = 0; t < T; ++t)
                     bulk_g2s(smem_u32(st + t * A_TILE_BYTES),
                              g.planes + (long long)t * g.plane_bytes + src_off, abytes,
                              full_a(s));
+                if (BPRE) {
+                    const long long b_src =
+                        pr.bt_off + ((long long)it * g.nct + ct) * B_TILE_BYTES;
+                    for (int t = 0; t < T; ++t)
+                        bulk_g2s(smem_u32(st + CF::BBF_OFF + t * B_TILE_BYTES),
+                                 g.bplanes + (long long)t * g.bplane_bytes + b_src,
+                                 B_TILE_BYTES, full_a(s));
+                }
             }
             __syncwarp();
-            if (lane < krows) {
+            if (!BPRE && lane < krows) {
                 const float* src =
                     g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase;
                 bulk_g2s(smem_u32(st + CF::RAW_OFF + lane * TN * 4), src, rbytes, full_a(s));
@@ -333,7 +352,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             for (int it = 0; it < nkt && ok; ++it) {
                 const int s = it % NS;
                 const uint32_t ph = (uint32_t)(it / NS) & 1u;
-                ok = mbar_wait(full_a(s), ph, abort_flag) && mbar_wait(full_b(s), ph, abort_flag);
+                ok = mbar_wait(full_a(s), ph, abort_flag) &&
+                     (BPRE || mbar_wait(full_b(s), ph, abort_flag));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = smem_u32(smem + s * CF::STAGE_BYTES);
@@ -379,7 +399,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             // the epilogue of all converter warps reads the table
             asm volatile("bar.sync 1, %0;" ::"r"(NCONV) : "memory");
         }
-        for (int it = 0; it < nkt; ++it) {
+        for (int it = 0; it < (BPRE ? 0 : nkt); ++it) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
             if (g.raw_bulk) {
@@ -510,9 +530,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     }
 }
 
-template <int T, bool F16>
+template <int T, bool F16, bool BPRE>
 __global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(const __grid_constant__ GemmArgs g) {
-    split_gemm_body<T, F16>(g, g.tiles[blockIdx.x]);
+    split_gemm_body<T, F16, BPRE>(g, g.tiles[blockIdx.x]);
 }
 
 // Grouped launch: tile.w is the plan's index in the group.
@@ -522,11 +542,64 @@ struct GemmGroup {
     const int4* tiles;
 };
 
-template <int T, bool F16>
+template <int T, bool F16, bool BPRE>
 __global__ void __launch_bounds__(NTHREADS, 2)
     split_gemm_group_kernel(const __grid_constant__ GemmGroup G) {
     const int4 t = G.tiles[blockIdx.x];
-    split_gemm_body<T, F16>(G.a[t.w], t);
+    split_gemm_body<T, F16, BPRE>(G.a[t.w], t);
+}
+
+// Split the FP32 operand B of every problem into T 16-bit terms, stored as
+// pre-tiled K-major B tiles (the layout the converters build in shared
+// memory): tile (problem, k-tile it, column tile ct) at
+// bt_off + (it nct + ct) * B_TILE_BYTES of each term plane.  Block (p, it);
+// thread unit (c, k8) reads 8 rows of column c (coalesced over c) and
+// writes 16 bytes per term.  FP16 scales each column as the GEMM's
+// converters do.
+template <int T, bool F16>
+__global__ void __launch_bounds__(256)
+    split_b_kernel(const float* __restrict__ B, const SplitProb* __restrict__ probs, int C,
+                   int nct, const unsigned* __restrict__ colmax, unsigned char* planes,
+                   long long plane_bytes) {
+    const SplitProb pr = probs[blockIdx.x];
+    const int it = blockIdx.y;
+    if (it >= pr.nkt) return;
+    const int k0 = it * TK;
+    const int cpad = nct * TN;
+    for (int u = threadIdx.x; u < cpad * (TK / 8); u += blockDim.x) {
+        const int c = u % cpad, k8 = u / cpad;
+        float x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + k8 * 8 + e;
+            x[e] = (k < pr.K && c < C) ? __ldg(B + pr.b_off + (long long)k * pr.b_stride + c)
+                                       : 0.f;
+        }
+        if (F16) {
+            const float cs = c < C ? col_scale(colmax[c]) : 1.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] *= cs;
+        }
+        const int ct = c / TN, cc = c % TN;
+        const long long off = pr.bt_off + ((long long)it * nct + ct) * B_TILE_BYTES +
+                              ((cc >> 3) * (TK / 8) + k8) * 128 + (cc & 7) * 16;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            float y[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                y[e] = round16<F16>(x[e]);
+                x[e] -= y[e];
+                if (F16 && t == 0) x[e] *= 2048.f;
+            }
+            uint4 pk;
+            pk.x = pack2<F16>(y[0], y[1]);
+            pk.y = pack2<F16>(y[2], y[3]);
+            pk.z = pack2<F16>(y[4], y[5]);
+            pk.w = pack2<F16>(y[6], y[7]);
+            *reinterpret_cast<uint4*>(planes + (long long)t * plane_bytes + off) = pk;
+        }
+    }
 }
 
 // Split the FP64 P~ table into T BF16 planes, pre-tiled (see top of file).
@@ -676,7 +749,7 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
     tf.clear();
     ti.clear();
     fwd_bytes = inv_bytes = 0;
-    long long fwd_rows = 0, inv_rows = 0;
+    long long fwd_rows = 0, inv_rows = 0, inv_bt = 0;
     const int nct = (C + TN - 1) / TN;
     for (int m = 0; m <= N; ++m) {
         for (int q = 0; q < 2; ++q) {
@@ -711,6 +784,9 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             inv_bytes += (long long)v.R8 * v.nkt * TK * 2;
             v.rs_off = inv_rows;
             inv_rows += v.R8;
+            v.bt_off = inv_bt;
+            inv_bt += (long long)v.nkt * nct * B_TILE_BYTES;
+            f.bt_off = 0;
             for (int mt = 0; mt * TM < Jh; ++mt)
                 for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, plan));
         }
@@ -732,14 +808,46 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.status = p->d_status;
     g.rs_inv = inverse ? st->rs_inv : st->rs_fwd;
     g.colmax = p->d_colmax ? p->d_colmax + (inverse ? g.C : 0) : nullptr;
+    g.nct = (g.C + TN - 1) / TN;
+    g.bplanes = inverse ? st->inv_bplanes : nullptr;
+    g.bplane_bytes = inverse ? (long long)st->inv_bplane_bytes : 0;
     return g;
 }
 
-template <int T, bool F16>
+template <int T, bool F16, bool BPRE>
 cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
-    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16>, Cfg<T>::SMEM);
+    constexpr int smem = Cfg<T, BPRE>::SMEM;
+    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16, BPRE>, smem);
     if (e) return e;
-    split_gemm_kernel<T, F16><<<ntiles, NTHREADS, Cfg<T>::SMEM, s>>>(g);
+    split_gemm_kernel<T, F16, BPRE><<<ntiles, NTHREADS, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+// Inverse B (the spectrum): column maxima for FP16, then the term planes.
+cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, cudaStream_t s) {
+    const SplitTables* st = p->split;
+    const int C = 2 * p->F, nct = (C + TN - 1) / TN;
+    cudaError_t e;
+    if (st->fp16 && (e = launch_colmax_inverse(p, spec, s))) return e;
+    const dim3 grid(2 * (p->N + 1), std::max(st->inv_max_nkt, 1));
+    const float* B = static_cast<const float*>(spec);
+    const unsigned* cm = p->d_colmax ? p->d_colmax + C : nullptr;
+    const long long pb = (long long)st->inv_bplane_bytes;
+    if (st->fp16) {
+        if (st->terms == 3)
+            split_b_kernel<3, true><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
+                                                         st->inv_bplanes, pb);
+        else
+            split_b_kernel<2, true><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
+                                                         st->inv_bplanes, pb);
+    } else {
+        if (st->terms == 3)
+            split_b_kernel<3, false><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
+                                                          st->inv_bplanes, pb);
+        else
+            split_b_kernel<2, false><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
+                                                          st->inv_bplanes, pb);
+    }
     return cudaGetLastError();
 }
 
@@ -749,17 +857,22 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
     const GemmArgs g = make_gemm_args(p, inverse, B, O);
     const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
     if (ntiles == 0) return cudaSuccess;
-    if (st->fp16) {
-        // forward: the FFT kernel gathered the column maxima of its output
-        if (inverse) {
-            const cudaError_t e = launch_colmax_inverse(p, B, s);
-            if (e) return e;
-        }
-        return st->terms == 3 ? gemm_launch<3, true>(g, ntiles, s)
-                              : gemm_launch<2, true>(g, ntiles, s);
+    if (inverse) {
+        // the spectrum is split once per call, then every row tile loads it
+        const cudaError_t e = launch_split_b_inverse(p, B, s);
+        if (e) return e;
+        if (st->fp16)
+            return st->terms == 3 ? gemm_launch<3, true, true>(g, ntiles, s)
+                                  : gemm_launch<2, true, true>(g, ntiles, s);
+        return st->terms == 3 ? gemm_launch<3, false, true>(g, ntiles, s)
+                              : gemm_launch<2, false, true>(g, ntiles, s);
     }
-    return st->terms == 3 ? gemm_launch<3, false>(g, ntiles, s)
-                          : gemm_launch<2, false>(g, ntiles, s);
+    // forward: the FFT kernel gathered the column maxima of its output (FP16)
+    if (st->fp16)
+        return st->terms == 3 ? gemm_launch<3, true, false>(g, ntiles, s)
+                              : gemm_launch<2, true, false>(g, ntiles, s);
+    return st->terms == 3 ? gemm_launch<3, false, false>(g, ntiles, s)
+                          : gemm_launch<2, false, false>(g, ntiles, s);
 }
 
 }  // namespace
@@ -800,6 +913,18 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
             return e;
         }
     }
+    {
+        const int nct = (C + TN - 1) / TN;
+        const SplitProb& last = pi.back();
+        st->inv_bplane_bytes =
+            (size_t)((last.bt_off + (long long)last.nkt * nct * B_TILE_BYTES + 255) / 256 * 256);
+        for (const SplitProb& v : pi) st->inv_max_nkt = std::max(st->inv_max_nkt, v.nkt);
+        if ((e = cudaMalloc(&st->inv_bplanes, st->inv_bplane_bytes * st->terms + 256)) !=
+            cudaSuccess) {
+            set_error("split spectrum planes: %s", cudaGetErrorString(e));
+            return e;
+        }
+    }
     // rows of A beyond R8 inside a 128-row tile are never copied; zero the
     // planes so K padding and row padding read as zero
     if ((e = cudaMemsetAsync(st->fwd_planes, 0, st->fwd_plane_bytes * st->terms, s)) ||
@@ -836,7 +961,8 @@ void split_tables_destroy(sht_plan_s* p) {
     SplitTables* st = p->split;
     if (!st) return;
     void* ptrs[] = {st->fwd_planes, st->inv_planes, st->d_probs_fwd, st->d_probs_inv,
-                    st->d_tiles_fwd, st->d_tiles_inv, st->rs_fwd, st->rs_inv, p->d_colmax};
+                    st->d_tiles_fwd, st->d_tiles_inv, st->rs_fwd, st->rs_inv, p->d_colmax,
+                    st->inv_bplanes};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete st;
@@ -865,11 +991,12 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
     for (auto& e : all) out.push_back(e.second);
 }
 
-template <int T, bool F16>
+template <int T, bool F16, bool BPRE>
 cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
-    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16>, Cfg<T>::SMEM);
+    constexpr int smem = Cfg<T, BPRE>::SMEM;
+    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16, BPRE>, smem);
     if (e) return e;
-    split_gemm_group_kernel<T, F16><<<ntiles, NTHREADS, Cfg<T>::SMEM, s>>>(G);
+    split_gemm_group_kernel<T, F16, BPRE><<<ntiles, NTHREADS, smem, s>>>(G);
     return cudaGetLastError();
 }
 
@@ -882,17 +1009,21 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
     G.tiles = tiles;
     for (int q = 0; q < n; ++q) G.a[q] = make_gemm_args(plans[q], inverse, in[q], out[q]);
     const SplitTables* st = plans[0]->split;
-    if (st->fp16 && inverse)
+    if (inverse)
         for (int q = 0; q < n; ++q) {
-            const cudaError_t e = launch_colmax_inverse(plans[q], in[q], s);
+            const cudaError_t e = launch_split_b_inverse(plans[q], in[q], s);
             if (e) return e;
         }
-    const int key = st->terms * 2 + (st->fp16 ? 1 : 0);
+    const int key = st->terms * 4 + (st->fp16 ? 2 : 0) + (inverse ? 1 : 0);
     switch (key) {
-        case 7: return group_launch<3, true>(G, ntiles, s);
-        case 5: return group_launch<2, true>(G, ntiles, s);
-        case 6: return group_launch<3, false>(G, ntiles, s);
-        default: return group_launch<2, false>(G, ntiles, s);
+        case 15: return group_launch<3, true, true>(G, ntiles, s);
+        case 14: return group_launch<3, true, false>(G, ntiles, s);
+        case 13: return group_launch<3, false, true>(G, ntiles, s);
+        case 12: return group_launch<3, false, false>(G, ntiles, s);
+        case 11: return group_launch<2, true, true>(G, ntiles, s);
+        case 10: return group_launch<2, true, false>(G, ntiles, s);
+        case 9: return group_launch<2, false, true>(G, ntiles, s);
+        default: return group_launch<2, false, false>(G, ntiles, s);
     }
 }
 
