@@ -273,7 +273,7 @@ def split_gemm_bytes(w, F, prec, inverse):
             d = w.N - m - q
             R = d // 2 + 1 if d >= 0 else 0
             if inverse:
-                tab += ((Jh + 7) // 8 * 8) * ((R + 15) // 16 * 16) * 2
+                tab += ((Jh - 1 + 7) // 8 * 8) * ((R + 15) // 16 * 16) * 2
             elif R:
                 tab += ((R + 7) // 8 * 8) * ((Jh + 15) // 16 * 16) * 2
     tab *= terms

@@ -240,6 +240,20 @@ __device__ __forceinline__ float round16(float x) {
         return __bfloat162float(__float2bfloat16_rn(x));
 }
 
+// One term of 8 values: x[e] rounded to 16 bits, packed in pairs; x keeps
+// the remainder x - term (exact, as the term is x rounded).
+template <bool F16>
+__device__ __forceinline__ uint4 split_term8(float (&x)[8]) {
+    float y[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        y[e] = round16<F16>(x[e]);
+        x[e] -= y[e];
+    }
+    return make_uint4(pack2<F16>(y[0], y[1]), pack2<F16>(y[2], y[3]), pack2<F16>(y[4], y[5]),
+                      pack2<F16>(y[6], y[7]));
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -435,18 +449,11 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 }
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    float y[8];
+                    const uint4 pk = split_term8<F16>(x);
+                    if (F16 && t == 0) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        y[e] = round16<F16>(x[e]);
-                        x[e] -= y[e];
-                        if (F16 && t == 0) x[e] *= 2048.f;   // x_2, x_3 carry weight 2^-11
+                        for (int e = 0; e < 8; ++e) x[e] *= 2048.f;   // x_2, x_3: weight 2^-11
                     }
-                    uint4 pk;
-                    pk.x = pack2<F16>(y[0], y[1]);
-                    pk.y = pack2<F16>(y[2], y[3]);
-                    pk.z = pack2<F16>(y[4], y[5]);
-                    pk.w = pack2<F16>(y[6], y[7]);
                     *reinterpret_cast<uint4*>(bst + t * B_TILE_BYTES + off) = pk;
                 }
             }
@@ -549,56 +556,93 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     split_gemm_body<T, F16, BPRE>(G.a[t.w], t);
 }
 
-// Split the FP32 operand B of every problem into T 16-bit terms, stored as
-// pre-tiled K-major B tiles (the layout the converters build in shared
-// memory): tile (problem, k-tile it, column tile ct) at
-// bt_off + (it nct + ct) * B_TILE_BYTES of each term plane.  Block (p, it);
-// thread unit (c, k8) reads 8 rows of column c (coalesced over c) and
-// writes 16 bytes per term.  FP16 scales each column as the GEMM's
-// converters do.
+// Split the FP32 operand B of every inverse problem (the spectrum rows of
+// one (m, parity)) into T 16-bit terms, stored as pre-tiled K-major B tiles
+// (the layout the converters build in shared memory): tile (problem,
+// k-tile it, column tile ct) at bt_off + (it nct + ct) * B_TILE_BYTES of
+// each term plane.  Block (problem, 32 columns); lane = column, warp w
+// takes the groups of 8 K rows g = w, w + 8, ... (reads coalesced over the
+// columns, 16 bytes written per term and group).  FP16 scales each column
+// as the GEMM's converters do.
+// The same pass computes the Equator row of the problem's output,
+// sum_r P~_{n_r}^m(0) X_{n_r}[c] (Eq. iLT at mu = 0), which the GEMM tiles
+// leave out: a compensated FP32 dot product (P~ as a float pair hi + lo,
+// exact products by FMA, two-sum accumulation) of the unscaled FP32
+// inputs, the 8 warps' partial sums combined in a fixed order.
+__device__ __forceinline__ void two_sum_acc(float& h, float& l, float a, float al) {
+    const float sum = __fadd_rn(h, a);
+    const float bp = __fsub_rn(sum, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bp)), __fsub_rn(a, bp));
+    h = sum;
+    l = __fadd_rn(l, __fadd_rn(err, al));
+}
+
 template <int T, bool F16>
 __global__ void __launch_bounds__(256)
     split_b_kernel(const float* __restrict__ B, const SplitProb* __restrict__ probs, int C,
                    int nct, const unsigned* __restrict__ colmax, unsigned char* planes,
-                   long long plane_bytes) {
-    const SplitProb pr = probs[blockIdx.x];
-    const int it = blockIdx.y;
-    if (it >= pr.nkt) return;
-    const int k0 = it * TK;
-    const int cpad = nct * TN;
-    for (int u = threadIdx.x; u < cpad * (TK / 8); u += blockDim.x) {
-        const int c = u % cpad, k8 = u / cpad;
+                   long long plane_bytes, const double* __restrict__ pnm, int ldp, int N,
+                   int Jh, float* __restrict__ O) {
+    extern __shared__ float2 peq[];   // [K] P~(0) of the problem's rows, (hi, lo)
+    __shared__ float2 red[8][32];
+    const int p = blockIdx.x;
+    const SplitProb pr = probs[p];
+    const size_t row0 = coef_offset(N, p >> 1) + (p & 1);
+    for (int k = threadIdx.x; k < pr.K; k += blockDim.x) {
+        const double v = pnm[(row0 + 2 * (size_t)k) * ldp + (Jh - 1)];
+        const float hi = (float)v;
+        peq[k] = make_float2(hi, (float)(v - (double)hi));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.y * 32 + lane;
+    const bool cin = c < C;
+    const float cs = (F16 && cin) ? col_scale(colmax[c]) : 1.f;
+    const int ct = c / TN, cc = c % TN;
+    float eh = 0.f, el = 0.f;
+    for (int g = w; g < pr.nkt * (TK / 8); g += 8) {
+        const int it = g / (TK / 8), k8 = g % (TK / 8);
         float x[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int k = k0 + k8 * 8 + e;
-            x[e] = (k < pr.K && c < C) ? __ldg(B + pr.b_off + (long long)k * pr.b_stride + c)
-                                       : 0.f;
+            const int k = g * 8 + e;
+            x[e] = (k < pr.K && cin) ? __ldg(B + pr.b_off + (long long)k * pr.b_stride + c)
+                                     : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = g * 8 + e;
+            if (k < pr.K) {
+                const float2 pe = peq[k];
+                const float ph = __fmul_rn(pe.x, x[e]);
+                two_sum_acc(eh, el, ph, fmaf(pe.y, x[e], fmaf(pe.x, x[e], -ph)));
+            }
         }
         if (F16) {
-            const float cs = c < C ? col_scale(colmax[c]) : 1.f;
 #pragma unroll
             for (int e = 0; e < 8; ++e) x[e] *= cs;
         }
-        const int ct = c / TN, cc = c % TN;
         const long long off = pr.bt_off + ((long long)it * nct + ct) * B_TILE_BYTES +
                               ((cc >> 3) * (TK / 8) + k8) * 128 + (cc & 7) * 16;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            float y[8];
+            const uint4 pk = split_term8<F16>(x);
+            if (F16 && t == 0) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                y[e] = round16<F16>(x[e]);
-                x[e] -= y[e];
-                if (F16 && t == 0) x[e] *= 2048.f;
+                for (int e = 0; e < 8; ++e) x[e] *= 2048.f;
             }
-            uint4 pk;
-            pk.x = pack2<F16>(y[0], y[1]);
-            pk.y = pack2<F16>(y[2], y[3]);
-            pk.z = pack2<F16>(y[4], y[5]);
-            pk.w = pack2<F16>(y[6], y[7]);
             *reinterpret_cast<uint4*>(planes + (long long)t * plane_bytes + off) = pk;
         }
+    }
+    red[w][lane] = make_float2(eh, el);
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int v = 1; v < 8; ++v) {
+            const float2 r = red[v][lane];
+            two_sum_acc(eh, el, r.x, r.y);
+        }
+        if (cin) O[pr.o_off + (long long)pr.Mrows * pr.o_stride + c] = __fadd_rn(eh, el);
     }
 }
 
@@ -621,7 +665,7 @@ __global__ void split_table_kernel(const double* __restrict__ pnm, int ldp, int 
         if (!inverse) {
             if (r < pr.Mrows && k < Jh) v = pnm[(row0 + 2 * (size_t)r) * ldp + k];
         } else {
-            if (r < Jh && k < pr.K) v = pnm[(row0 + 2 * (size_t)k) * ldp + r];
+            if (r < pr.Mrows && k < pr.K) v = pnm[(row0 + 2 * (size_t)k) * ldp + r];
         }
         const int kt = k / TK, kk = k % TK;
         const long long off = pr.a_off + (long long)kt * pr.R8 * TK * 2 +
@@ -650,7 +694,7 @@ __global__ void split_table_f16_kernel(const double* __restrict__ pnm, int ldp, 
     const long long K32 = (long long)pr.nkt * TK;
     auto aval = [&](int r, int k) -> double {
         if (!inverse) return (r < pr.Mrows && k < Jh) ? pnm[(row0 + 2 * (size_t)r) * ldp + k] : 0.0;
-        return (r < Jh && k < pr.K) ? pnm[(row0 + 2 * (size_t)k) * ldp + r] : 0.0;
+        return (r < pr.Mrows && k < pr.K) ? pnm[(row0 + 2 * (size_t)k) * ldp + r] : 0.0;
     };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int r = warp; r < pr.R8; r += nw) {
@@ -771,10 +815,12 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             fwd_rows += f.R8;
             for (int mt = 0; mt * TM < R; ++mt)
                 for (int c = 0; c < nct; ++c) tf.push_back(make_int4(2 * m + q, mt, c, plan));
+            // inverse rows: the nodes north of the Equator; the Equator row
+            // (node Jh - 1) is computed by split_b_kernel
             SplitProb& v = pi[2 * m + q];
             v.a_off = inv_bytes;
-            v.R8 = (Jh + 7) / 8 * 8;
-            v.Mrows = Jh;
+            v.R8 = (Jh - 1 + 7) / 8 * 8;
+            v.Mrows = Jh - 1;
             v.K = R;
             v.nkt = (R + TK - 1) / TK;
             v.b_off = row0 * C;
@@ -787,7 +833,7 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             v.bt_off = inv_bt;
             inv_bt += (long long)v.nkt * nct * B_TILE_BYTES;
             f.bt_off = 0;
-            for (int mt = 0; mt * TM < Jh; ++mt)
+            for (int mt = 0; mt * TM < Jh - 1; ++mt)
                 for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, plan));
         }
     }
@@ -824,30 +870,30 @@ cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
 }
 
 // Inverse B (the spectrum): column maxima for FP16, then the term planes.
-cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, cudaStream_t s) {
+cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, void* work,
+                                   cudaStream_t s) {
     const SplitTables* st = p->split;
     const int C = 2 * p->F, nct = (C + TN - 1) / TN;
     cudaError_t e;
     if (st->fp16 && (e = launch_colmax_inverse(p, spec, s))) return e;
-    const dim3 grid(2 * (p->N + 1), std::max(st->inv_max_nkt, 1));
+    const dim3 grid(2 * (p->N + 1), nct * (TN / 32));
+    const size_t smem = (size_t)std::max(st->inv_max_nkt, 1) * TK * sizeof(float2);
     const float* B = static_cast<const float*>(spec);
+    float* O = static_cast<float*>(work);
     const unsigned* cm = p->d_colmax ? p->d_colmax + C : nullptr;
     const long long pb = (long long)st->inv_bplane_bytes;
+#define SHT_SPLIT_B(TT, FF)                                                                    \
+    split_b_kernel<TT, FF><<<grid, 256, smem, s>>>(B, st->d_probs_inv, C, nct, cm,             \
+                                                   st->inv_bplanes, pb, p->d_pnm, p->ldp,      \
+                                                   p->N, p->Jh, O)
     if (st->fp16) {
-        if (st->terms == 3)
-            split_b_kernel<3, true><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
-                                                         st->inv_bplanes, pb);
-        else
-            split_b_kernel<2, true><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
-                                                         st->inv_bplanes, pb);
+        if (st->terms == 3) SHT_SPLIT_B(3, true);
+        else SHT_SPLIT_B(2, true);
     } else {
-        if (st->terms == 3)
-            split_b_kernel<3, false><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
-                                                          st->inv_bplanes, pb);
-        else
-            split_b_kernel<2, false><<<grid, 256, 0, s>>>(B, st->d_probs_inv, C, nct, cm,
-                                                          st->inv_bplanes, pb);
+        if (st->terms == 3) SHT_SPLIT_B(3, false);
+        else SHT_SPLIT_B(2, false);
     }
+#undef SHT_SPLIT_B
     return cudaGetLastError();
 }
 
@@ -856,11 +902,11 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
     const SplitTables* st = p->split;
     const GemmArgs g = make_gemm_args(p, inverse, B, O);
     const int ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
-    if (ntiles == 0) return cudaSuccess;
     if (inverse) {
         // the spectrum is split once per call, then every row tile loads it
-        const cudaError_t e = launch_split_b_inverse(p, B, s);
-        if (e) return e;
+        // (this pass also writes the Equator row, which no tile covers)
+        const cudaError_t e = launch_split_b_inverse(p, B, O, s);
+        if (e || ntiles == 0) return e;
         if (st->fp16)
             return st->terms == 3 ? gemm_launch<3, true, true>(g, ntiles, s)
                                   : gemm_launch<2, true, true>(g, ntiles, s);
@@ -868,6 +914,7 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
                               : gemm_launch<2, false, true>(g, ntiles, s);
     }
     // forward: the FFT kernel gathered the column maxima of its output (FP16)
+    if (ntiles == 0) return cudaSuccess;
     if (st->fp16)
         return st->terms == 3 ? gemm_launch<3, true, false>(g, ntiles, s)
                               : gemm_launch<2, true, false>(g, ntiles, s);
@@ -1003,7 +1050,6 @@ cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
 cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
                                const void* const* in, void* const* out, const int4* tiles,
                                int ntiles, cudaStream_t s) {
-    if (ntiles == 0) return cudaSuccess;
     GemmGroup G;
     G.n = n;
     G.tiles = tiles;
@@ -1011,9 +1057,10 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
     const SplitTables* st = plans[0]->split;
     if (inverse)
         for (int q = 0; q < n; ++q) {
-            const cudaError_t e = launch_split_b_inverse(plans[q], in[q], s);
+            const cudaError_t e = launch_split_b_inverse(plans[q], in[q], out[q], s);
             if (e) return e;
         }
+    if (ntiles == 0) return cudaSuccess;
     const int key = st->terms * 4 + (st->fp16 ? 2 : 0) + (inverse ? 1 : 0);
     switch (key) {
         case 15: return group_launch<3, true, true>(G, ntiles, s);
