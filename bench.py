@@ -45,6 +45,8 @@ def parse_args():
                     help="field-levels per GPU (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plan's default launch shapes")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the FP64 comparison path")
     return ap.parse_args()
@@ -339,6 +341,8 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     import torch
     from paper_1711_11296_gb300 import sht, workloads as W
     plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device)
+    # launch shapes picked by the library's autotuner (plan setup, untimed)
+    tuning = plan.tuning if args.no_autotune else plan.autotune(reps=2)
     a = W.workload_spectrum(w, F=F, field0=rank * F)
     spec_in = torch.from_numpy(a).to(device=device, dtype=plan.complex_dtype)
     grid = plan.empty_grid()
@@ -372,7 +376,8 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     barrier(dist, local)
     ms = max_over_ranks(dist, ms_local, device)
     res = {"ms": ms, "prof": prof, "clocks": clocks,
-           "launches": sum(n for _, n in prof.values())}
+           "launches": sum(n for _, n in prof.values()),
+           "tuning": {k: v for k, v in tuning.items() if k != "ms_per_pair"}}
 
     if e2e_wanted:
         host_in = torch.from_numpy(a).to(plan.complex_dtype).pin_memory()
@@ -457,6 +462,7 @@ def native_arm(args):
             "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
                        "field_levels_per_gpu": F, "path": prec,
                        "parallelism": "replicas" if world > 1 else "single",
+                       "launch_shapes": head.get("tuning"),
                        "l2": "inputs larger than L2 (grid %.1f GB)"
                              % (F * w.J * w.I * (8 if prec == "fp64" else 4) / 1e9)},
             "roofline": roof, "stages": stages, "fp64_path": other,

@@ -184,6 +184,34 @@ int sht_group_inverse(sht_group_t group, const void* const* specs, void* const* 
  * otherwise.  Clears the recorded status. */
 int sht_plan_status(sht_plan_t plan);
 
+/* Launch shapes (no counterpart in the paper; they change speed, never a
+ * result).  fields_per_cta: fields whose latitude rows one FFT CTA
+ * transforms (1..min(nfields, 64), within 227 KB of shared memory).
+ * tile_width: column-tile width of the split tensor-core GEMMs, 64 or 128
+ * (split plans only; SHT_ERR_UNSUPPORTED for FP64).  A value of 0 leaves
+ * that shape unchanged.  Changing the tile width synchronises the device
+ * and reallocates the plan's tile lists; groups created before then
+ * reject the plan (SHT_ERR_ARG) until they are recreated.  Not to be
+ * called while the plan has work in flight on another stream. */
+int sht_plan_set_tuning(sht_plan_t plan, int fields_per_cta, int tile_width);
+
+/* Current launch shapes; tile_width is 0 for FP64 plans.  Either pointer
+ * may be NULL. */
+int sht_plan_get_tuning(sht_plan_t plan, int* fields_per_cta, int* tile_width);
+
+/* Autotuner: time `reps` (1..1000) inverse + forward pairs per candidate on
+ * `stream`, using the plan's workspace and temporary device buffers of one
+ * grid and one spectrum (zero fields), first over the fields-per-CTA
+ * values 1, 2, 3, 4, 5, 6, 8, 10, 12, 16 that fit, then over the tile
+ * widths 128 and 64 (split plans), and keep the fastest.  The choice is
+ * remembered for the process per (device, N, J, I, nfields, precision):
+ * a later call for the same shape applies it without timing.  Outputs
+ * (host, may be NULL): the chosen shapes and the mean milliseconds of a
+ * pair under them.  Synchronous; SHT_ERR_ALLOC if the buffers cannot be
+ * allocated.  The plan must not be in use on another stream meanwhile. */
+int sht_plan_autotune(sht_plan_t plan, int reps, void* stream, int* fields_per_cta,
+                      int* tile_width, float* ms_per_pair);
+
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
  * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,

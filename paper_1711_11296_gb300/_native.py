@@ -17,6 +17,7 @@ EXPORTED = [
     "sht_profile_enable", "sht_profile_read", "sht_last_error", "sht_version",
     "sht_forward_noalloc", "sht_plan_status", "sht_group_create",
     "sht_group_destroy", "sht_group_forward", "sht_group_inverse",
+    "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -64,6 +65,9 @@ def _load():
     lib.sht_group_destroy.argtypes = [vp]
     lib.sht_group_forward.argtypes = [vp, vpp, vpp, vp]
     lib.sht_group_inverse.argtypes = [vp, vpp, vpp, vp]
+    lib.sht_plan_set_tuning.argtypes = [vp, i, i]
+    lib.sht_plan_get_tuning.argtypes = [vp, ip, ip]
+    lib.sht_plan_autotune.argtypes = [vp, i, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
     lib.sht_last_error.restype = ctypes.c_char_p
     lib.sht_version.restype = ctypes.c_char_p
     for name in EXPORTED:

@@ -26,6 +26,8 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
                                const void* const* in, void* const* out, const int4* tiles,
                                int ntiles, cudaStream_t s);
 
+int split_tile_width(const sht_plan_s* p);
+
 constexpr uint64_t kGroupMagic = 0x53485447'524F5550ull;   // "SHTGROUP"
 
 }  // namespace sht
@@ -36,6 +38,7 @@ struct sht_group_s {
     int prec;
     int device;
     sht_plan_s* plans[sht::kMaxGroup];
+    int tile_width;   // split plans: the GEMM tile width the tile lists were built for
     int4* d_tiles_fwd;
     int ntiles_fwd;
     int4* d_tiles_inv;
@@ -118,6 +121,10 @@ extern "C" int sht_group_create(const sht_plan_t* plans, int nplans, sht_group_t
                 set_error("plan %d appears twice (its workspace cannot be shared)", q);
                 return SHT_ERR_ARG;
             }
+        if (split_tile_width(plans[q]) != split_tile_width(plans[0])) {
+            set_error("plans of a group must share the GEMM tile width");
+            return SHT_ERR_ARG;
+        }
     }
     sht_group_s* g = new (std::nothrow) sht_group_s();
     if (!g) {
@@ -127,6 +134,7 @@ extern "C" int sht_group_create(const sht_plan_t* plans, int nplans, sht_group_t
     g->n = nplans;
     g->prec = plans[0]->prec;
     g->device = plans[0]->device;
+    g->tile_width = split_tile_width(plans[0]);
     for (int q = 0; q < nplans; ++q) g->plans[q] = plans[q];
     std::vector<int4> tf, ti;
     if (g->prec == SHT_FP64) {
@@ -193,6 +201,10 @@ int check_group(sht_group_t g, const void* const* a, const void* const* b) {
         if (!plan_is_live(g->plans[q])) {
             set_error("plan %d of the group was destroyed", q);
             return SHT_ERR_HANDLE;
+        }
+        if (split_tile_width(g->plans[q]) != g->tile_width) {
+            set_error("plan %d changed its GEMM tile width after the group was created", q);
+            return SHT_ERR_ARG;
         }
     }
     if (!a || !b) {

@@ -59,6 +59,7 @@ struct SplitProb {
 
 struct SplitTables {
     int terms = 3;
+    int tn = 128;                 // column-tile width of the GEMMs (64 or 128)
     bool fp16 = false;
     float* rs_fwd = nullptr;      // FP16 plans: 1 / row scale of each A row
     float* rs_inv = nullptr;
@@ -78,30 +79,44 @@ struct SplitTables {
 
 namespace {
 
-constexpr int TM = 128, TN = 128, TK = 16, UK = 16;
+constexpr int TM = 128, TK = 16, UK = 16;
+constexpr int TN_MAX = 128;                // column tiles are TN = 64 or 128 wide
 constexpr int NCONV = 256;                 // converter / epilogue threads (8 warps)
 constexpr int NTHREADS = NCONV + 64;       // + bulk-copy warp + MMA warp
 constexpr int WARP_PRODUCER = NCONV / 32, WARP_MMA = NCONV / 32 + 1;
 constexpr int A_TILE_BYTES = TM * TK * 2;   // one term
-constexpr int B_TILE_BYTES = TN * TK * 2;
-constexpr int RAW_BYTES = TK * TN * 4;      // FP32 staging of B: TK rows of TN
 constexpr uint32_t kSBO = (TK / 8) * 128;   // stride between 8-row core groups
-constexpr int TMEM_COLS = 2 * TN;     // two 128 x TN FP32 accumulators
 constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
+
+// Per column-tile width TN: one 16-bit B tile (TK x TN), the FP32 staging of
+// B (TK rows of TN) and the tensor memory of the two TN-column accumulators.
+template <int TN> struct Wid {
+    static constexpr int B_TILE_BYTES = TN * TK * 2;
+    static constexpr int RAW_BYTES = TK * TN * 4;
+    static constexpr int TMEM_COLS = 2 * TN;
+    static constexpr int CTAS_PER_SM = TN == 64 ? 3 : 2;
+};
 
 // Stage layout: T A tiles | FP32 staging of B | T 16-bit B tiles.  With B
 // split beforehand (BPRE) a stage is T A tiles | T B tiles, both copied in
-// by the bulk-copy warp, and the pipeline is deeper.
-template <int T, bool BPRE = false> struct Cfg {
-    // <= 113 KB: two CTAs per SM
+// by the bulk-copy warp, and the pipeline is deeper.  Stage counts keep
+// TN = 128 under 113 KB (two CTAs per SM, 2 x 256 TMEM columns) and TN = 64
+// under 75 KB (three CTAs per SM, 3 x 128 columns).
+template <int T, bool BPRE, int TN> struct Cfg {
     static constexpr int NS = BPRE ? (T == 3 ? 4 : 6) : (T == 3 ? 3 : 4);
     static constexpr int RAW_OFF = T * A_TILE_BYTES;
-    static constexpr int BBF_OFF = RAW_OFF + (BPRE ? 0 : RAW_BYTES);
-    static constexpr int STAGE_BYTES = BBF_OFF + T * B_TILE_BYTES;
+    static constexpr int BBF_OFF = RAW_OFF + (BPRE ? 0 : Wid<TN>::RAW_BYTES);
+    static constexpr int STAGE_BYTES = BBF_OFF + T * Wid<TN>::B_TILE_BYTES;
     static constexpr int BAR_OFF = NS * STAGE_BYTES;
     static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
     static constexpr int SMEM = CSI_OFF + TN * 4;
 };
+static_assert(Cfg<3, false, 128>::SMEM <= 113 * 1024 && Cfg<2, false, 128>::SMEM <= 113 * 1024 &&
+                  Cfg<3, true, 128>::SMEM <= 113 * 1024 && Cfg<2, true, 128>::SMEM <= 113 * 1024,
+              "two CTAs per SM at TN = 128");
+static_assert(Cfg<3, false, 64>::SMEM <= 75 * 1024 && Cfg<2, false, 64>::SMEM <= 75 * 1024 &&
+                  Cfg<3, true, 64>::SMEM <= 75 * 1024 && Cfg<2, true, 64>::SMEM <= 75 * 1024,
+              "three CTAs per SM at TN = 64");
 
 struct GemmArgs {
     const unsigned char* planes;   // term t plane at planes + t * plane_bytes
@@ -194,19 +209,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B,
-// both K-major, N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 accumulator (bit 4), A and B
+// BF16 (format 1 at bits 7 and 10) or FP16 (format 0), both K-major,
+// N = TN (N/8 at bit 17), M = 128 (M/16 at bit 24).
+template <bool F16, int TN>
+constexpr uint32_t idesc_f16() {
+    return (1u << 4) | (F16 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(TN >> 3) << 17) |
+           ((uint32_t)(TM >> 4) << 24);
+}
 
-// The same with FP16 A and B (format 0 in both fields).
-constexpr uint32_t kIdescF16 = (1u << 4) | ((uint32_t)(TN >> 3) << 17) |
-                               ((uint32_t)(TM >> 4) << 24);
-
-template <bool F16>
+template <bool F16, int TN>
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b,
                                         uint32_t accum) {
-    const uint32_t idesc = F16 ? kIdescF16 : kIdesc;
+    constexpr uint32_t idesc = idesc_f16<F16, TN>();
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
@@ -274,9 +289,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 extern __shared__ __align__(1024) unsigned char split_smem[];
 
-template <int T, bool F16, bool BPRE>
+template <int T, bool F16, bool BPRE, int TN>
 __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 tile) {
-    using CF = Cfg<T, BPRE>;
+    using CF = Cfg<T, BPRE, TN>;
+    constexpr int B_TILE_BYTES = Wid<TN>::B_TILE_BYTES;
+    constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
     constexpr int NS = CF::NS;
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
@@ -388,7 +405,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                             const bool lead = (a == 0 && b == 0);
                             const uint32_t acc =
                                 (it > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
-                            mma_f16<F16>(lead ? tmem : tmem + TN, ad, bd, acc);
+                            mma_f16<F16, TN>(lead ? tmem : tmem + TN, ad, bd, acc);
                         }
                     }
                 }
@@ -426,8 +443,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             unsigned char* bst = stg + CF::BBF_OFF;
             const int k0 = it * TK;
 #pragma unroll
-            for (int v = 0; v < (TN * TK / 8) / NCONV; ++v) {
-                const int u = tid + NCONV * v;
+            for (int u = tid; u < TN * TK / 8; u += NCONV) {
                 const int c = u % TN;
                 const int k8 = u / TN;
                 const int cg = cbase + c;
@@ -537,9 +553,10 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     }
 }
 
-template <int T, bool F16, bool BPRE>
-__global__ void __launch_bounds__(NTHREADS, 2) split_gemm_kernel(const __grid_constant__ GemmArgs g) {
-    split_gemm_body<T, F16, BPRE>(g, g.tiles[blockIdx.x]);
+template <int T, bool F16, bool BPRE, int TN>
+__global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
+    split_gemm_kernel(const __grid_constant__ GemmArgs g) {
+    split_gemm_body<T, F16, BPRE, TN>(g, g.tiles[blockIdx.x]);
 }
 
 // Grouped launch: tile.w is the plan's index in the group.
@@ -549,11 +566,11 @@ struct GemmGroup {
     const int4* tiles;
 };
 
-template <int T, bool F16, bool BPRE>
-__global__ void __launch_bounds__(NTHREADS, 2)
+template <int T, bool F16, bool BPRE, int TN>
+__global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
     split_gemm_group_kernel(const __grid_constant__ GemmGroup G) {
     const int4 t = G.tiles[blockIdx.x];
-    split_gemm_body<T, F16, BPRE>(G.a[t.w], t);
+    split_gemm_body<T, F16, BPRE, TN>(G.a[t.w], t);
 }
 
 // Split the FP32 operand B of every inverse problem (the spectrum rows of
@@ -577,12 +594,13 @@ __device__ __forceinline__ void two_sum_acc(float& h, float& l, float a, float a
     l = __fadd_rn(l, __fadd_rn(err, al));
 }
 
-template <int T, bool F16>
+template <int T, bool F16, int TN>
 __global__ void __launch_bounds__(256)
     split_b_kernel(const float* __restrict__ B, const SplitProb* __restrict__ probs, int C,
                    int nct, const unsigned* __restrict__ colmax, unsigned char* planes,
                    long long plane_bytes, const double* __restrict__ pnm, int ldp, int N,
                    int Jh, float* __restrict__ O) {
+    constexpr int B_TILE_BYTES = Wid<TN>::B_TILE_BYTES;
     extern __shared__ float2 peq[];   // [K] P~(0) of the problem's rows, (hi, lo)
     __shared__ float2 red[8][32];
     const int p = blockIdx.x;
@@ -784,7 +802,7 @@ int terms_of(int prec) { return (prec == SHT_BF16X2 || prec == SHT_FP16X2) ? 2 :
 
 // Problems (one per (m, parity)) and tiles of both directions for
 // truncation N, Jh northern nodes and C real columns; tile.w = plan.
-void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& pf,
+void build_split_lists(int N, int Jh, int C, int tn, int plan, std::vector<SplitProb>& pf,
                        std::vector<SplitProb>& pi, std::vector<int4>& tf,
                        std::vector<int4>& ti, long long& fwd_bytes, long long& inv_bytes) {
     const int nprob = 2 * (N + 1);
@@ -794,7 +812,7 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
     ti.clear();
     fwd_bytes = inv_bytes = 0;
     long long fwd_rows = 0, inv_rows = 0, inv_bt = 0;
-    const int nct = (C + TN - 1) / TN;
+    const int nct = (C + tn - 1) / tn;
     for (int m = 0; m <= N; ++m) {
         for (int q = 0; q < 2; ++q) {
             const int d = N - m - q;
@@ -831,7 +849,7 @@ void build_split_lists(int N, int Jh, int C, int plan, std::vector<SplitProb>& p
             v.rs_off = inv_rows;
             inv_rows += v.R8;
             v.bt_off = inv_bt;
-            inv_bt += (long long)v.nkt * nct * B_TILE_BYTES;
+            inv_bt += (long long)v.nkt * nct * tn * TK * 2;
             f.bt_off = 0;
             for (int mt = 0; mt * TM < Jh - 1; ++mt)
                 for (int c = 0; c < nct; ++c) ti.push_back(make_int4(2 * m + q, mt, c, plan));
@@ -854,46 +872,62 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.status = p->d_status;
     g.rs_inv = inverse ? st->rs_inv : st->rs_fwd;
     g.colmax = p->d_colmax ? p->d_colmax + (inverse ? g.C : 0) : nullptr;
-    g.nct = (g.C + TN - 1) / TN;
+    g.nct = (g.C + st->tn - 1) / st->tn;
     g.bplanes = inverse ? st->inv_bplanes : nullptr;
     g.bplane_bytes = inverse ? (long long)st->inv_bplane_bytes : 0;
     return g;
 }
 
-template <int T, bool F16, bool BPRE>
+template <int T, bool F16, bool BPRE, int TN>
 cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
-    constexpr int smem = Cfg<T, BPRE>::SMEM;
-    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16, BPRE>, smem);
+    constexpr int smem = Cfg<T, BPRE, TN>::SMEM;
+    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16, BPRE, TN>, smem);
     if (e) return e;
-    split_gemm_kernel<T, F16, BPRE><<<ntiles, NTHREADS, smem, s>>>(g);
+    split_gemm_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(g);
     return cudaGetLastError();
+}
+
+// Variant index: bit 0 three terms, bit 1 FP16, bit 2 pre-split B, bit 3 TN = 64.
+int variant(int terms, bool f16, bool bpre, int tn) {
+    return (terms == 3 ? 1 : 0) | (f16 ? 2 : 0) | (bpre ? 4 : 0) | (tn == 64 ? 8 : 0);
+}
+
+#define SHT_VARIANTS(F)                                                                       \
+    {F<2, false, false, 128>, F<3, false, false, 128>, F<2, true, false, 128>,                \
+     F<3, true, false, 128>,  F<2, false, true, 128>,  F<3, false, true, 128>,                \
+     F<2, true, true, 128>,   F<3, true, true, 128>,   F<2, false, false, 64>,                \
+     F<3, false, false, 64>,  F<2, true, false, 64>,   F<3, true, false, 64>,                 \
+     F<2, false, true, 64>,   F<3, false, true, 64>,   F<2, true, true, 64>,                  \
+     F<3, true, true, 64>}
+
+cudaError_t launch_gemm_variant(int v, const GemmArgs& g, int ntiles, cudaStream_t s) {
+    using Fn = cudaError_t (*)(const GemmArgs&, int, cudaStream_t);
+    static const Fn tab[16] = SHT_VARIANTS(gemm_launch);
+    return tab[v](g, ntiles, s);
 }
 
 // Inverse B (the spectrum): column maxima for FP16, then the term planes.
 cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, void* work,
                                    cudaStream_t s) {
     const SplitTables* st = p->split;
-    const int C = 2 * p->F, nct = (C + TN - 1) / TN;
+    const int C = 2 * p->F, nct = (C + st->tn - 1) / st->tn;
     cudaError_t e;
     if (st->fp16 && (e = launch_colmax_inverse(p, spec, s))) return e;
-    const dim3 grid(2 * (p->N + 1), nct * (TN / 32));
+    const dim3 grid(2 * (p->N + 1), nct * (st->tn / 32));
     const size_t smem = (size_t)std::max(st->inv_max_nkt, 1) * TK * sizeof(float2);
     const float* B = static_cast<const float*>(spec);
     float* O = static_cast<float*>(work);
     const unsigned* cm = p->d_colmax ? p->d_colmax + C : nullptr;
     const long long pb = (long long)st->inv_bplane_bytes;
-#define SHT_SPLIT_B(TT, FF)                                                                    \
-    split_b_kernel<TT, FF><<<grid, 256, smem, s>>>(B, st->d_probs_inv, C, nct, cm,             \
-                                                   st->inv_bplanes, pb, p->d_pnm, p->ldp,      \
-                                                   p->N, p->Jh, O)
-    if (st->fp16) {
-        if (st->terms == 3) SHT_SPLIT_B(3, true);
-        else SHT_SPLIT_B(2, true);
-    } else {
-        if (st->terms == 3) SHT_SPLIT_B(3, false);
-        else SHT_SPLIT_B(2, false);
-    }
-#undef SHT_SPLIT_B
+    using Fn = void (*)(const float*, const SplitProb*, int, int, const unsigned*,
+                        unsigned char*, long long, const double*, int, int, int, float*);
+    static const Fn tab[8] = {split_b_kernel<2, false, 128>, split_b_kernel<3, false, 128>,
+                              split_b_kernel<2, true, 128>,  split_b_kernel<3, true, 128>,
+                              split_b_kernel<2, false, 64>,  split_b_kernel<3, false, 64>,
+                              split_b_kernel<2, true, 64>,   split_b_kernel<3, true, 64>};
+    const Fn k = tab[(variant(st->terms, st->fp16, false, st->tn) & 3) | (st->tn == 64 ? 4 : 0)];
+    k<<<grid, 256, smem, s>>>(B, st->d_probs_inv, C, nct, cm, st->inv_bplanes, pb, p->d_pnm,
+                              p->ldp, p->N, p->Jh, O);
     return cudaGetLastError();
 }
 
@@ -907,19 +941,11 @@ cudaError_t launch_gemm(const sht_plan_s* p, bool inverse, const void* B, void* 
         // (this pass also writes the Equator row, which no tile covers)
         const cudaError_t e = launch_split_b_inverse(p, B, O, s);
         if (e || ntiles == 0) return e;
-        if (st->fp16)
-            return st->terms == 3 ? gemm_launch<3, true, true>(g, ntiles, s)
-                                  : gemm_launch<2, true, true>(g, ntiles, s);
-        return st->terms == 3 ? gemm_launch<3, false, true>(g, ntiles, s)
-                              : gemm_launch<2, false, true>(g, ntiles, s);
+        return launch_gemm_variant(variant(st->terms, st->fp16, true, st->tn), g, ntiles, s);
     }
     // forward: the FFT kernel gathered the column maxima of its output (FP16)
     if (ntiles == 0) return cudaSuccess;
-    if (st->fp16)
-        return st->terms == 3 ? gemm_launch<3, true, false>(g, ntiles, s)
-                              : gemm_launch<2, true, false>(g, ntiles, s);
-    return st->terms == 3 ? gemm_launch<3, false, false>(g, ntiles, s)
-                          : gemm_launch<2, false, false>(g, ntiles, s);
+    return launch_gemm_variant(variant(st->terms, st->fp16, false, st->tn), g, ntiles, s);
 }
 
 }  // namespace
@@ -935,7 +961,7 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
     std::vector<SplitProb> pf, pi;
     std::vector<int4> tf, ti;
     long long fwd_bytes = 0, inv_bytes = 0;
-    build_split_lists(N, Jh, C, 0, pf, pi, tf, ti, fwd_bytes, inv_bytes);
+    build_split_lists(N, Jh, C, TN_MAX, 0, pf, pi, tf, ti, fwd_bytes, inv_bytes);
     st->fwd_plane_bytes = (size_t)(fwd_bytes + 255) / 256 * 256;
     st->inv_plane_bytes = (size_t)(inv_bytes + 255) / 256 * 256;
     st->ntiles_fwd = (int)tf.size();
@@ -961,10 +987,12 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
         }
     }
     {
-        const int nct = (C + TN - 1) / TN;
+        // laid out for the widest tiles: the 64-wide layout needs no more
+        const int nct = (C + TN_MAX - 1) / TN_MAX;
         const SplitProb& last = pi.back();
-        st->inv_bplane_bytes =
-            (size_t)((last.bt_off + (long long)last.nkt * nct * B_TILE_BYTES + 255) / 256 * 256);
+        st->inv_bplane_bytes = (size_t)((last.bt_off +
+                                         (long long)last.nkt * nct * Wid<TN_MAX>::B_TILE_BYTES +
+                                         255) / 256 * 256);
         for (const SplitProb& v : pi) st->inv_max_nkt = std::max(st->inv_max_nkt, v.nkt);
         if ((e = cudaMalloc(&st->inv_bplanes, st->inv_bplane_bytes * st->terms + 256)) !=
             cudaSuccess) {
@@ -1017,6 +1045,46 @@ void split_tables_destroy(sht_plan_s* p) {
     p->d_colmax = nullptr;
 }
 
+// Rebuild the tile lists of a split plan for column tiles TN = tn (64 or
+// 128).  The term planes and row scales do not depend on the width; the
+// pre-split spectrum planes were sized for the widest tiles.  Synchronises
+// the device: kernels in flight may still read the old lists.
+cudaError_t split_set_tile_width(sht_plan_s* p, int tn) {
+    SplitTables* st = p->split;
+    if (!st || (tn != 64 && tn != 128)) return cudaErrorInvalidValue;
+    if (st->tn == tn) return cudaSuccess;
+    std::vector<SplitProb> pf, pi;
+    std::vector<int4> tf, ti;
+    long long fb = 0, ib = 0;
+    build_split_lists(p->N, p->Jh, 2 * p->F, tn, 0, pf, pi, tf, ti, fb, ib);
+    int4 *dtf = nullptr, *dti = nullptr;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMalloc(&dtf, (tf.size() + 1) * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc(&dti, (ti.size() + 1) * sizeof(int4));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dtf, tf.data(), tf.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(dti, ti.data(), ti.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(st->d_probs_inv, pi.data(), pi.size() * sizeof(SplitProb),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (dtf) cudaFree(dtf);
+        if (dti) cudaFree(dti);
+        return e;
+    }
+    cudaFree(st->d_tiles_fwd);
+    cudaFree(st->d_tiles_inv);
+    st->d_tiles_fwd = dtf;
+    st->d_tiles_inv = dti;
+    st->ntiles_fwd = (int)tf.size();
+    st->ntiles_inv = (int)ti.size();
+    st->tn = tn;
+    return cudaSuccess;
+}
+
+int split_tile_width(const sht_plan_s* p) { return p->split ? p->split->tn : 0; }
+
 // Tiles of a group of split plans (same term count), heaviest first: every
 // tile's K loop has nkt steps.  Returns the host list.
 void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vector<int4>& out) {
@@ -1026,7 +1094,7 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
         std::vector<SplitProb> pf, pi;
         std::vector<int4> tf, ti;
         long long fb, ib;
-        build_split_lists(p->N, p->Jh, 2 * p->F, q, pf, pi, tf, ti, fb, ib);
+        build_split_lists(p->N, p->Jh, 2 * p->F, p->split->tn, q, pf, pi, tf, ti, fb, ib);
         const std::vector<SplitProb>& pr = inverse ? pi : pf;
         for (const int4& t : inverse ? ti : tf) all.push_back({pr[t.x].nkt, t});
     }
@@ -1038,12 +1106,12 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
     for (auto& e : all) out.push_back(e.second);
 }
 
-template <int T, bool F16, bool BPRE>
+template <int T, bool F16, bool BPRE, int TN>
 cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
-    constexpr int smem = Cfg<T, BPRE>::SMEM;
-    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16, BPRE>, smem);
+    constexpr int smem = Cfg<T, BPRE, TN>::SMEM;
+    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16, BPRE, TN>, smem);
     if (e) return e;
-    split_gemm_group_kernel<T, F16, BPRE><<<ntiles, NTHREADS, smem, s>>>(G);
+    split_gemm_group_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(G);
     return cudaGetLastError();
 }
 
@@ -1061,17 +1129,9 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
             if (e) return e;
         }
     if (ntiles == 0) return cudaSuccess;
-    const int key = st->terms * 4 + (st->fp16 ? 2 : 0) + (inverse ? 1 : 0);
-    switch (key) {
-        case 15: return group_launch<3, true, true>(G, ntiles, s);
-        case 14: return group_launch<3, true, false>(G, ntiles, s);
-        case 13: return group_launch<3, false, true>(G, ntiles, s);
-        case 12: return group_launch<3, false, false>(G, ntiles, s);
-        case 11: return group_launch<2, true, true>(G, ntiles, s);
-        case 10: return group_launch<2, true, false>(G, ntiles, s);
-        case 9: return group_launch<2, false, true>(G, ntiles, s);
-        default: return group_launch<2, false, false>(G, ntiles, s);
-    }
+    using Fn = cudaError_t (*)(const GemmGroup&, int, cudaStream_t);
+    static const Fn tab[16] = SHT_VARIANTS(group_launch);
+    return tab[variant(st->terms, st->fp16, inverse, st->tn)](G, ntiles, s);
 }
 
 cudaError_t launch_legendre_fwd_split(const sht_plan_s* p, const void* work, void* spec,

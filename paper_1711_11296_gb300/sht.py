@@ -126,6 +126,30 @@ class Plan:
         bounded wait since the last check."""
         check(lib.sht_plan_status(self._h))
 
+    # -- launch shapes ----------------------------------------------------
+    @property
+    def tuning(self):
+        """{"fields_per_cta": G, "tile_width": TN} (TN is 0 for FP64 plans)."""
+        g, t = ctypes.c_int(), ctypes.c_int()
+        check(lib.sht_plan_get_tuning(self._h, ctypes.byref(g), ctypes.byref(t)))
+        return {"fields_per_cta": g.value, "tile_width": t.value}
+
+    def set_tuning(self, fields_per_cta=0, tile_width=0):
+        """Set the FFT fields per CTA and/or the split GEMM tile width (64 or
+        128); 0 leaves a shape unchanged.  Results do not depend on either."""
+        with torch.cuda.device(self.device):
+            check(lib.sht_plan_set_tuning(self._h, int(fields_per_cta), int(tile_width)))
+
+    def autotune(self, reps=3):
+        """Time the candidate launch shapes on this plan and keep the fastest;
+        returns the choice and the mean ms of an inverse + forward pair."""
+        g, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        with torch.cuda.device(self.device):
+            check(lib.sht_plan_autotune(self._h, int(reps), _stream_ptr(self.device),
+                                        ctypes.byref(g), ctypes.byref(t), ctypes.byref(ms)))
+        return {"fields_per_cta": g.value, "tile_width": t.value,
+                "ms_per_pair": ms.value}
+
     def profile(self, on=True):
         """Turn per-launch event timing on or off."""
         check(lib.sht_profile_enable(self._h, 1 if on else 0))
