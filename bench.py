@@ -163,7 +163,14 @@ def fft_bytes(w, F, real_bytes):
 # field-levels.  Writes still held in L2 when a launch ends are not counted
 # by the capture.  Keyed by (stage, path, workload, field-levels); an entry
 # is removed whenever its kernel changes and re-added from a new capture.
+_SCALE_T319x64_TO_T639x256 = (256 * 1281 * 2560) / (64 * 641 * 1280)
+_FFT_INV_T319x64 = (105.07776 + 151.479552) * 1e6   # bytes, fft_inverse<float, 640>
+_FFT_FWD_T319x64 = (210.19776 + 69.801984) * 1e6    # bytes, fft_forward<float, 640>
 MEASURED_TRAFFIC = {}
+for _p in ("bf16x3", "bf16x2", "fp16x3", "fp16x2"):   # the same FP32 inverse FFT
+    MEASURED_TRAFFIC[("fft_inverse", _p, "T639", 256)] = _FFT_INV_T319x64 * _SCALE_T319x64_TO_T639x256
+for _p in ("bf16x3", "bf16x2"):   # FP16 plans add column maxima to the forward FFT
+    MEASURED_TRAFFIC[("fft_forward", _p, "T639", 256)] = _FFT_FWD_T319x64 * _SCALE_T319x64_TO_T639x256
 
 
 def peaks():
