@@ -387,30 +387,61 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
            "tuning": {k: v for k, v in tuning.items() if k != "ms_per_pair"}}
 
     if e2e_wanted:
-        host_in = torch.from_numpy(a).to(plan.complex_dtype).pin_memory()
-        host_out = torch.empty_like(host_in).pin_memory()
-        dev_in = torch.empty_like(spec_in)
+        # End to end through the public API with host buffers: every step
+        # uploads its input spectrum from pinned host memory, runs the
+        # inverse and forward transforms and downloads the resulting
+        # spectrum.  Copies run on their own streams, double-buffered, so that
+        # step i+1's upload and step i-1's download overlap step i's compute.
+        host_in = [torch.from_numpy(a).to(plan.complex_dtype).pin_memory() for _ in range(2)]
+        host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
+        dev_in = [torch.empty_like(spec_in) for _ in range(2)]
+        dev_out = [torch.empty_like(spec_out) for _ in range(2)]
+        up, down = torch.cuda.Stream(device), torch.cuda.Stream(device)
+        computed = [torch.cuda.Event() for _ in range(2)]
+        uploaded = [torch.cuda.Event() for _ in range(2)]
+        downloaded = [torch.cuda.Event() for _ in range(2)]
+        for e in computed + downloaded:
+            e.record(stream)
 
-        def e2e_step():
-            dev_in.copy_(host_in, non_blocking=True)
-            plan.inverse(dev_in, out=grid)
-            plan.forward(grid, out=spec_out)
-            host_out.copy_(spec_out, non_blocking=True)
+        def upload(i):
+            b = i % 2
+            up.wait_event(computed[b])            # step i-2 no longer reads dev_in[b]
+            with torch.cuda.stream(up):
+                dev_in[b].copy_(host_in[b], non_blocking=True)
+                uploaded[b].record(up)
 
-        for _ in range(max(args.warmup, 1)):
-            e2e_step()
+        def e2e_steps(n):
+            up.wait_stream(stream)                # nothing starts before the timer
+            upload(0)
+            for i in range(n):
+                b = i % 2
+                if i + 1 < n:
+                    upload(i + 1)
+                stream.wait_event(uploaded[b])
+                stream.wait_event(downloaded[b])  # step i-2's result is out of dev_out[b]
+                plan.inverse(dev_in[b], out=grid)
+                plan.forward(grid, out=dev_out[b])
+                computed[b].record(stream)
+                down.wait_event(computed[b])
+                with torch.cuda.stream(down):
+                    host_out[b].copy_(dev_out[b], non_blocking=True)
+                    downloaded[b].record(down)
+            stream.wait_stream(down)
+
+        e2e_steps(max(args.warmup, 1))
         torch.cuda.synchronize()
         barrier(dist, local)
         ev0.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_steps(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
-        nbytes = host_in.numel() * host_in.element_size()
+        nbytes = host_in[0].numel() * host_in[0].element_size()
         res["e2e"] = {"value": world * F * args.steps / (e2e_ms / 1000.0),
                       "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                      "d2h_bytes_per_step": nbytes}
+                      "d2h_bytes_per_step": nbytes,
+                      "copies": "pinned host buffers, double-buffered on copy streams "
+                                "overlapping the neighbouring steps' compute"}
     plan.close()
     del spec_in, grid, spec_out
     torch.cuda.empty_cache()
