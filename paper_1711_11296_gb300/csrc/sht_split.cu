@@ -82,8 +82,8 @@ namespace {
 constexpr int TM = 128, TK = 16, UK = 16;
 constexpr int TN_MAX = 128;                // column tiles are TN = 64 or 128 wide
 constexpr int NCONV = 256;                 // converter / epilogue threads (8 warps)
-constexpr int NTHREADS = NCONV + 64;       // + bulk-copy warp + MMA warp
-constexpr int WARP_PRODUCER = NCONV / 32, WARP_MMA = NCONV / 32 + 1;
+constexpr int NTHREADS = NCONV + 96;       // + bulk-copy warp + MMA warp + B-row copy warp
+constexpr int WARP_PRODUCER = NCONV / 32, WARP_MMA = NCONV / 32 + 1, WARP_RAW = NCONV / 32 + 2;
 constexpr int A_TILE_BYTES = TM * TK * 2;   // one term
 constexpr uint32_t kSBO = (TK / 8) * 128;   // stride between 8-row core groups
 constexpr long long kWaitCycles = 4LL << 30;   // ~2 s at 2 GHz
@@ -97,17 +97,20 @@ template <int TN> struct Wid {
     static constexpr int CTAS_PER_SM = TN == 64 ? 3 : 2;
 };
 
-// Stage layout: T A tiles | FP32 staging of B | T 16-bit B tiles.  With B
-// split beforehand (BPRE) a stage is T A tiles | T B tiles, both copied in
-// by the bulk-copy warp, and the pipeline is deeper.  Stage counts keep
+// Stage layout: T A tiles | T 16-bit B tiles, in a ring of NS stages.  When
+// the GEMM converts B itself (not BPRE), the FP32 rows of B arrive in a
+// separate ring of NR slots (TK rows of TN each), filled by their own copy
+// warp and freed as soon as the converters have read them, so the long-
+// latency FP32 rows run further ahead than the A tiles.  Stage counts keep
 // TN = 128 under 113 KB (two CTAs per SM, 2 x 256 TMEM columns) and TN = 64
 // under 75 KB (three CTAs per SM, 3 x 128 columns).
 template <int T, bool BPRE, int TN> struct Cfg {
     static constexpr int NS = BPRE ? (T == 3 ? 4 : 6) : (T == 3 ? 3 : 4);
-    static constexpr int RAW_OFF = T * A_TILE_BYTES;
-    static constexpr int BBF_OFF = RAW_OFF + (BPRE ? 0 : Wid<TN>::RAW_BYTES);
+    static constexpr int NR = BPRE ? 0 : (T == 3 ? 4 : 5);
+    static constexpr int BBF_OFF = T * A_TILE_BYTES;
     static constexpr int STAGE_BYTES = BBF_OFF + T * Wid<TN>::B_TILE_BYTES;
-    static constexpr int BAR_OFF = NS * STAGE_BYTES;
+    static constexpr int RAW_OFF = NS * STAGE_BYTES;   // raw slot r at RAW_OFF + r RAW_BYTES
+    static constexpr int BAR_OFF = RAW_OFF + NR * Wid<TN>::RAW_BYTES;
     static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
     static constexpr int SMEM = CSI_OFF + TN * 4;
 };
@@ -295,12 +298,14 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     constexpr int B_TILE_BYTES = Wid<TN>::B_TILE_BYTES;
     constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
     constexpr int NS = CF::NS;
+    constexpr int NR = CF::NR;
+    constexpr int NB = 3 * NS + 2 * NR + 1;   // barriers
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
-    // bars: full_a[NS], full_b[NS], empty[NS], done
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1));
+    // bars: full_a[NS], full_b[NS], empty[NS], full_r[NR], empty_r[NR], done
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * NB);
     volatile int* abort_flag =
-        reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * (3 * NS + 1) + 8);
+        reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * NB + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SplitProb pr = g.probs[tile.x];
@@ -310,13 +315,19 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     auto full_a = [&](int s) { return bar0 + 8u * s; };
     auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
     auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
-    const uint32_t done = bar0 + 8u * (3 * NS);
+    auto full_r = [&](int r) { return bar0 + 8u * (3 * NS + r); };
+    auto empty_r = [&](int r) { return bar0 + 8u * (3 * NS + NR + r); };
+    const uint32_t done = bar0 + 8u * (3 * NS + 2 * NR);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(full_a(s), 1);
             mbar_init(full_b(s), NCONV);
             mbar_init(empty(s), 1);
+        }
+        for (int r = 0; r < NR; ++r) {
+            mbar_init(full_r(r), 1);
+            mbar_init(empty_r(r), NCONV);
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -336,11 +347,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
 
     const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
     if (warp == WARP_PRODUCER) {
-        // ---- producer: A tiles (lane 0) and the FP32 rows of B (lane k) ----
+        // ---- producer: A tiles (and pre-split B tiles), lane 0 ----
         const uint32_t abytes = (uint32_t)h * TK * 2;
-        const int cbase = ct * TN;
-        const int ccopy = min(TN, g.C - cbase);            // valid columns
-        const uint32_t rbytes = (uint32_t)ccopy * 4u;
         for (int it = 0; it < nkt; ++it) {
             const int s = it % NS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
@@ -348,12 +356,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             if (lane == 0) ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
-            const int k0 = it * TK;
-            const int krows = (!BPRE && g.raw_bulk) ? max(0, min(TK, pr.K - k0)) : 0;
             unsigned char* st = smem + s * CF::STAGE_BYTES;
             if (lane == 0) {
-                mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES)
-                                                             : rbytes * (uint32_t)krows));
+                mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES) : 0u));
                 const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
                                           (long long)mt * TM * TK * 2;
                 for (int t = 0; t < T; ++t)
@@ -370,10 +375,32 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 }
             }
             __syncwarp();
-            if (!BPRE && lane < krows) {
-                const float* src =
-                    g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase;
-                bulk_g2s(smem_u32(st + CF::RAW_OFF + lane * TN * 4), src, rbytes, full_a(s));
+        }
+    } else if (warp == WARP_RAW) {
+        // ---- the FP32 rows of B (lane k copies row k of a stage) into the
+        // raw ring, NR stages ahead of the converters ----
+        if (!BPRE && g.raw_bulk) {
+            const int cbase = ct * TN;
+            const int ccopy = min(TN, g.C - cbase);   // valid columns
+            const uint32_t rbytes = (uint32_t)ccopy * 4u;
+            for (int it = 0; it < nkt; ++it) {
+                const int r = it % (NR > 0 ? NR : 1);
+                const uint32_t ph = (uint32_t)(it / (NR > 0 ? NR : 1)) & 1u;
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(empty_r(r), ph ^ 1u, abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
+                const int k0 = it * TK;
+                const int krows = max(0, min(TK, pr.K - k0));
+                if (lane == 0) mbar_expect_tx(full_r(r), rbytes * (uint32_t)krows);
+                __syncwarp();
+                if (lane < krows) {
+                    const float* src =
+                        g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase;
+                    bulk_g2s(smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES + lane * TN * 4),
+                             src, rbytes, full_r(r));
+                }
+                __syncwarp();
             }
         }
     } else if (warp == WARP_MMA) {
@@ -430,16 +457,17 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             // the epilogue of all converter warps reads the table
             asm volatile("bar.sync 1, %0;" ::"r"(NCONV) : "memory");
         }
+        constexpr int NRS = NR > 0 ? NR : 1;
         for (int it = 0; it < (BPRE ? 0 : nkt); ++it) {
-            const int s = it % NS;
+            const int s = it % NS, r = it % NRS;
             const uint32_t ph = (uint32_t)(it / NS) & 1u;
-            if (g.raw_bulk) {
-                if (!mbar_wait(full_a(s), ph, abort_flag)) break;
-            } else {
-                if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
-            }
+            // the stage's B-term area is free once the MMAs of its previous
+            // use are done; the FP32 rows wait in raw slot r
+            if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+            if (g.raw_bulk && !mbar_wait(full_r(r), (uint32_t)(it / NRS) & 1u, abort_flag)) break;
             unsigned char* stg = smem + s * CF::STAGE_BYTES;
-            const float* raw = reinterpret_cast<const float*>(stg + CF::RAW_OFF);
+            const float* raw =
+                reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
             unsigned char* bst = stg + CF::BBF_OFF;
             const int k0 = it * TK;
 #pragma unroll
@@ -475,6 +503,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(full_b(s));
+            if (g.raw_bulk) mbar_arrive(empty_r(r));
         }
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the tile
         // rows it may access) for column half w / 4 ----
