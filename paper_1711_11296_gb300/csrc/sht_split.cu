@@ -106,7 +106,7 @@ template <int TN> struct Wid {
 // under 75 KB (three CTAs per SM, 3 x 128 columns).
 template <int T, bool BPRE, int TN> struct Cfg {
     static constexpr int NS = BPRE ? (T == 3 ? 4 : 6) : (T == 3 ? 3 : 4);
-    static constexpr int NR = BPRE ? 0 : (T == 3 ? 4 : 5);
+    static constexpr int NR = BPRE ? 0 : (T == 3 ? 5 : 6);
     static constexpr int BBF_OFF = T * A_TILE_BYTES;
     static constexpr int STAGE_BYTES = BBF_OFF + T * Wid<TN>::B_TILE_BYTES;
     static constexpr int RAW_OFF = NS * STAGE_BYTES;   // raw slot r at RAW_OFF + r RAW_BYTES
@@ -221,6 +221,16 @@ constexpr uint32_t idesc_f16() {
            ((uint32_t)(TM >> 4) << 24);
 }
 
+// The same MMA with the instruction descriptor in a register (N chosen per tile).
+__device__ __forceinline__ void mma_f16_rt(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 template <bool F16, int TN>
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b,
                                         uint32_t accum) {
@@ -299,6 +309,12 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
     constexpr int NS = CF::NS;
     constexpr int NR = CF::NR;
+    // Forward with 128-wide column tiles: the product is formed transposed,
+    // D^T = B^T A^T, with the 128 columns of B on the MMA's M side and the
+    // tile's A rows (at most 128, rounded up to 16) on its N side, so a
+    // partial row tile issues only the MMA work of its rows.  TMEM lanes are
+    // then columns and TMEM columns rows.
+    constexpr bool SWAP = !BPRE && TN == 128;
     constexpr int NB = 3 * NS + 2 * NR + 1;   // barriers
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
@@ -406,6 +422,12 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     } else if (warp == WARP_MMA) {
         // ---- MMA issuer ----
         if (lane == 0) {
+            // SWAP: M = 128 (the column tile), N = the tile's A rows rounded to 16
+            const int nrows = ((min(TM, pr.R8 - TM * mt) + 15) / 16) * 16;
+            const uint32_t idesc_swap = (1u << 4) | (F16 ? 0u : ((1u << 7) | (1u << 10))) |
+                                        ((uint32_t)(nrows >> 3) << 17) |
+                                        ((uint32_t)(TM >> 4) << 24);
+            (void)idesc_swap;
             bool ok = true;
             for (int it = 0; it < nkt && ok; ++it) {
                 const int s = it % NS;
@@ -432,7 +454,10 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                             const bool lead = (a == 0 && b == 0);
                             const uint32_t acc =
                                 (it > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
-                            mma_f16<F16, TN>(lead ? tmem : tmem + TN, ad, bd, acc);
+                            if constexpr (SWAP)
+                                mma_f16_rt(lead ? tmem : tmem + TN, bd, ad, idesc_swap, acc);
+                            else
+                                mma_f16<F16, TN>(lead ? tmem : tmem + TN, ad, bd, acc);
                         }
                     }
                 }
@@ -510,8 +535,55 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         const bool have = nkt > 0;
         bool ok = true;
         if (have) ok = mbar_wait(done, 0, abort_flag);
+        // the TMEM loads and shuffles below are warp-collective: agree on ok
+        ok = __all_sync(0xffffffffu, ok) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int lq = warp & 3, half = warp >> 2;
+        if constexpr (SWAP) {
+            // TMEM lane 32 lq + lane = column c of the tile; TMEM columns =
+            // rows n.  For each row the 32 lanes store 32 adjacent columns.
+            const int c = cbase + 32 * lq + lane;
+            const bool col_ok = c < g.C && ok && !*abort_flag;
+            const float csi = (F16 && c < g.C) ? col_unscale(g.colmax[c]) : 0.f;
+            constexpr int NCH = TN / 16 / (NCONV / 128);
+            for (int cc = 0; cc < NCH; ++cc) {
+                const int ch = half * NCH + cc;
+                const int n0 = TM * mt + ch * 16;
+                if (n0 >= pr.Mrows) break;   // uniform over the warp
+                uint32_t r[16];
+                if (have && ok) {
+                    uint32_t r2[16];
+                    const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
+                    tmem_ld16(ta, r);
+                    tmem_ld16(ta + TN, r2);
+                    // FP16: lane k < 16 fetches the row scale of row n0 + k
+                    const int nl = n0 + (lane & 15);
+                    const float my_rsi =
+                        (F16 && nl < pr.Mrows) ? g.rs_inv[pr.rs_off + nl] : 0.f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        float v;
+                        if (F16) {
+                            const float rsi = __shfl_sync(0xffffffffu, my_rsi, k);
+                            v = (__uint_as_float(r[k]) + __uint_as_float(r2[k]) * (1.f / 2048.f)) *
+                                rsi * csi;
+                        } else {
+                            v = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
+                        }
+                        r[k] = __float_as_uint(v);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) r[k] = 0u;
+                }
+                if (!col_ok) continue;
+                float* ocol = g.O + pr.o_off + c;
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (n0 + k < pr.Mrows)
+                        ocol[(long long)(n0 + k) * pr.o_stride] = __uint_as_float(r[k]);
+            }
+        } else {
         const int row = TM * mt + 32 * lq + lane;
         const bool row_ok = row < pr.Mrows && ok && !*abort_flag;
         float* orow = g.O + pr.o_off + (long long)row * pr.o_stride;
@@ -562,6 +634,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 for (int i = 0; i < 16; ++i)
                     if (c0 + i < g.C) orow[c0 + i] = __uint_as_float(r[i]);
             }
+        }
         }
     }
     if (*abort_flag && threadIdx.x == 0 && g.status) atomicOr(g.status, 1);
