@@ -247,39 +247,33 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b,
 // remainder scaled by 2^11 so that it keeps FP16's precision:
 // x_2 = fp16(2^11 (x - x_1)), x_3 = fp16(2^11 (x - x_1) - x_2), so that
 // x = x_1 + 2^-11 (x_2 + x_3) + O(2^-35).
-template <bool F16>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi);
-template <>
-__device__ __forceinline__ uint32_t pack2<false>(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-template <>
-__device__ __forceinline__ uint32_t pack2<true>(float lo, float hi) {
-    __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-template <bool F16>
-__device__ __forceinline__ float round16(float x) {
-    if constexpr (F16)
-        return __half2float(__float2half_rn(x));
-    else
-        return __bfloat162float(__float2bfloat16_rn(x));
-}
-
-// One term of 8 values: x[e] rounded to 16 bits, packed in pairs; x keeps
-// the remainder x - term (exact, as the term is x rounded).
-template <bool F16>
+// One term of 8 values: x[e] rounded to 16 bits, packed in pairs (one
+// packed conversion per pair); unless it is the last term, x keeps the
+// remainder x - term (exact, as the term is x rounded), formed from the
+// packed bits without a second conversion.
+template <bool F16, bool LAST>
 __device__ __forceinline__ uint4 split_term8(float (&x)[8]) {
-    float y[8];
+    uint32_t w[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        y[e] = round16<F16>(x[e]);
-        x[e] -= y[e];
+    for (int i = 0; i < 4; ++i) {
+        if constexpr (F16) {
+            const __half2 h = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t*>(&h);
+            if (!LAST) {
+                const float2 f = __half22float2(h);
+                x[2 * i] -= f.x;
+                x[2 * i + 1] -= f.y;
+            }
+        } else {
+            const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t*>(&b);
+            if (!LAST) {
+                x[2 * i] -= __uint_as_float(w[i] << 16);
+                x[2 * i + 1] -= __uint_as_float(w[i] & 0xffff0000u);
+            }
+        }
     }
-    return make_uint4(pack2<F16>(y[0], y[1]), pack2<F16>(y[2], y[3]), pack2<F16>(y[4], y[5]),
-                      pack2<F16>(y[6], y[7]));
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -518,7 +512,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 }
 #pragma unroll
                 for (int t = 0; t < T; ++t) {
-                    const uint4 pk = split_term8<F16>(x);
+                    const uint4 pk = t == T - 1 ? split_term8<F16, true>(x)
+                                                : split_term8<F16, false>(x);
                     if (F16 && t == 0) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) x[e] *= 2048.f;   // x_2, x_3: weight 2^-11
@@ -746,7 +741,7 @@ __global__ void __launch_bounds__(256)
                               ((cc >> 3) * (TK / 8) + k8) * 128 + (cc & 7) * 16;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const uint4 pk = split_term8<F16>(x);
+            const uint4 pk = t == T - 1 ? split_term8<F16, true>(x) : split_term8<F16, false>(x);
             if (F16 && t == 0) {
 #pragma unroll
                 for (int e = 0; e < 8; ++e) x[e] *= 2048.f;
