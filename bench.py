@@ -159,18 +159,18 @@ def fft_bytes(w, F, real_bytes):
 
 # DRAM traffic per launch of the kernels that dominate a step, from ncu
 # captures (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel
-# code on the T319 x 64 field-level case, scaled by grid points x
-# field-levels.  Writes still held in L2 when a launch ends are not counted
-# by the capture.  Keyed by (stage, path, workload, field-levels); an entry
-# is removed whenever its kernel changes and re-added from a new capture.
-_SCALE_T319x64_TO_T639x256 = (256 * 1281 * 2560) / (64 * 641 * 1280)
-_FFT_INV_T319x64 = (105.07776 + 151.479552) * 1e6   # bytes, fft_inverse<float, 640>
-_FFT_FWD_T319x64 = (210.19776 + 69.801984) * 1e6    # bytes, fft_forward<float, 640>
+# code at the T639 shape with 64 field-levels (the same per-CTA work as the
+# 256-field workload), scaled by the field count.  Writes still held in L2
+# when a launch ends are not counted by the capture.  Keyed by (stage, path,
+# workload, field-levels); an entry is removed whenever its kernel changes
+# and re-added from a new capture.
+_FFT_INV_T639x64 = (419.847 + 784.076) * 1e6   # bytes, fft_inverse<float, 1280>
+_FFT_FWD_T639x64 = (839.795 + 389.227) * 1e6   # bytes, fft_forward<float, 1280>
 MEASURED_TRAFFIC = {}
 for _p in ("bf16x3", "bf16x2", "fp16x3", "fp16x2"):   # the same FP32 inverse FFT
-    MEASURED_TRAFFIC[("fft_inverse", _p, "T639", 256)] = _FFT_INV_T319x64 * _SCALE_T319x64_TO_T639x256
+    MEASURED_TRAFFIC[("fft_inverse", _p, "T639", 256)] = _FFT_INV_T639x64 * 256 / 64
 for _p in ("bf16x3", "bf16x2"):   # FP16 plans add column maxima to the forward FFT
-    MEASURED_TRAFFIC[("fft_forward", _p, "T639", 256)] = _FFT_FWD_T319x64 * _SCALE_T319x64_TO_T639x256
+    MEASURED_TRAFFIC[("fft_forward", _p, "T639", 256)] = _FFT_FWD_T639x64 * 256 / 64
 
 
 def peaks():
@@ -338,8 +338,8 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
     t = MEASURED_TRAFFIC.get((name, prec, w.name, F))
     if t is not None:
         roof["traffic"] = t
-        roof["traffic_note"] = ("ncu DRAM bytes of the T319 x 64 capture scaled to this "
-                                "workload; writes still in L2 at the end of a launch "
+        roof["traffic_note"] = ("ncu DRAM bytes of the T639 x 64 capture scaled by the "
+                                "field count; writes still in L2 at the end of a launch "
                                 "are not counted")
     return roof
 
