@@ -11,6 +11,10 @@ GPU library: the two share no code.
 Contents (all FP64 except the binary128 Legendre recurrence of Sec. 4.1):
 
 * ``cc_nodes``, ``cc_weights``     -- Eq. (cc-points), Eq. (cc-wgt)
+* ``fejer1_nodes``, ``fejer1_weights``, ``analysis_fejer1``,
+  ``synthesis_fejer1``             -- the shifted grid of Fejer's first
+                                      rule, Sec. 3.3 (Eq. fejer1-points and
+                                      the interpolatory form of Eq. fejer1-wgt)
 * ``gauss_nodes_weights``          -- Eq. (gauss-quad)/(gauss-wgt) by the
                                       Golub-Welsch eigenproblem
 * ``pnm_cc``, ``pnm_at``           -- P~_n^m by the recurrence in binary128

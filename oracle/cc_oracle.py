@@ -33,7 +33,8 @@ __all__ = [
     "pnm_cc", "pnm_at", "dft_forward", "dft_inverse", "analysis",
     "synthesis", "adjoint_analysis", "adjoint_synthesis", "restrict_nested",
     "analysis_gauss", "synthesis_gauss", "legendre_forward_m",
-    "legendre_inverse_m", "nested_rows",
+    "legendre_inverse_m", "nested_rows", "fejer1_nodes", "fejer1_weights",
+    "analysis_fejer1", "synthesis_fejer1",
 ]
 
 _lib = None
@@ -97,6 +98,32 @@ def cc_weights(J):
     s = np.sin(np.pi * r / (J + 1))
     sin_t = np.sin(np.pi * j[:, 0] / (J + 1))
     return 4.0 * sin_t / (J + 1) * (s / p).sum(axis=1)
+
+
+def fejer1_nodes(J):
+    """Nodes of Fejer's first rule on the shifted grid, Eq. (fejer1-points).
+
+    Returns (theta, mu, sin_theta) for j = 1..J, theta_j = (j - 1/2) pi / J,
+    j = 1 northernmost."""
+    j = np.arange(1, J + 1, dtype=np.float64)
+    theta = np.pi * (2.0 * j - 1.0) / (2.0 * J)
+    return theta, np.cos(theta), np.sin(theta)
+
+
+def fejer1_weights(J):
+    """Weights of Fejer's first rule by its explicit cosine sum (Sec. 3.3):
+
+        w_j = (2/J) (1 - 2 sum_{p=1}^{floor(J/2)} cos(2 p theta_j)/(4p^2 - 1)).
+
+    Eq. (fejer1-wgt) is printed without the factor 2 in front of the sum;
+    only with it is the rule interpolatory (exact to degree J-1), which the
+    tests pin.  Each cos(2 p theta_j) = cos(pi p (2j-1)/J) is evaluated
+    after reducing the integer p (2j-1) modulo 2J."""
+    j = np.arange(1, J + 1, dtype=np.int64)[:, None]
+    p = np.arange(1, J // 2 + 1, dtype=np.int64)[None, :]
+    r = (p * (2 * j - 1)) % (2 * J)
+    c = np.cos(np.pi * r / J)
+    return 2.0 / J * (1.0 - 2.0 * (c / (4.0 * p * p - 1.0)).sum(axis=1))
 
 
 def gauss_nodes_weights(J):
@@ -274,6 +301,27 @@ def synthesis_rows(spec, N, J, I, rows):
         a = spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
         X[:, :, m] = legendre_inverse_m(a, pnm_cc(N, J, m, m, j=rows))
     return dft_inverse(X, I)
+
+
+def analysis_fejer1(x, N):
+    """Forward SHT on the shifted grid of Fejer's first rule (Sec. 3.3): the
+    zonal DFT, then the quadrature with the weights of ``fejer1_weights`` at
+    the nodes of ``fejer1_nodes``.  x: real [F][J][I] (j = 1 first)."""
+    x = np.asarray(x, dtype=np.float64)
+    F, J, I = x.shape
+    _, mu, s = fejer1_nodes(J)
+    d = _analysis_general(x, N, lambda m: pnm_at(N, mu, s, m, m), fejer1_weights(J))
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m, a in d.items():
+        spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
+    return spec
+
+
+def synthesis_fejer1(spec, N, J, I):
+    """Inverse SHT (Eq. iSHT) evaluated on the J-point shifted grid."""
+    _, mu, s = fejer1_nodes(J)
+    return _synthesis_general(np.asarray(spec, np.complex128), N, J, I,
+                              lambda m: pnm_at(N, mu, s, m, m))
 
 
 def analysis_gauss(x, N):
