@@ -39,6 +39,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="T639")
+    ap.add_argument("--grid", default="cc", choices=["cc", "fejer1"],
+                    help="latitude grid: Clenshaw-Curtis or the shifted grid of "
+                         "Fejer's first rule")
     ap.add_argument("--precision", default="auto",
                     help="auto (headline path), fp64, bf16x3, ...")
     ap.add_argument("--fields", type=int, default=0,
@@ -347,7 +350,7 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
 def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     import torch
     from paper_1711_11296_gb300 import sht, workloads as W
-    plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device)
+    plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid=args.grid)
     # launch shapes picked by the library's autotuner (plan setup, untimed)
     tuning = plan.tuning if args.no_autotune else plan.autotune(reps=2)
     a = W.workload_spectrum(w, F=F, field0=rank * F)
@@ -498,7 +501,7 @@ def native_arm(args):
             "dtype": "f64" if prec == "fp64" else "f32+" + prec,
             "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
-                       "field_levels_per_gpu": F, "path": prec,
+                       "field_levels_per_gpu": F, "path": prec, "grid": args.grid,
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch_shapes": head.get("tuning"),
                        "l2": "inputs larger than L2 (grid %.1f GB)"

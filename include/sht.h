@@ -86,6 +86,27 @@ typedef enum {
 int sht_plan_create(int N, int J, int I, int nfields, int precision,
                     sht_plan_t* out);
 
+/* Latitude grids. */
+typedef enum {
+    SHT_GRID_CC = 0,     /* Clenshaw-Curtis (Fejer's second rule), Eq. (cc-points),
+                            weights Eq. (cc-wgt); nests K in 2K+1 (Sec. 3.2) */
+    SHT_GRID_FEJER1 = 1  /* shifted equispaced grid of Fejer's first rule
+                            (Sec. 3.3), theta_j = (j - 1/2) pi / J, Eq. (fejer1-points);
+                            weights w_j = (2/J)(1 - 2 sum_{p=1}^{floor(J/2)}
+                            cos(2 p theta_j)/(4p^2 - 1)): the interpolatory rule,
+                            exact to degree J-1 (J for odd J).  Eq. (fejer1-wgt)
+                            as printed lacks the factor 2 and is not exact. */
+} sht_grid;
+
+/* sht_plan_create on a chosen latitude grid (a sht_grid); everything else
+ * as sht_plan_create.  On SHT_GRID_FEJER1 the plan has the same layouts,
+ * precisions and entry points, with the same exactness condition
+ * J >= 2N+1, except sht_restrict_nested: that grid does not nest
+ * (Sec. 3.3), so it returns SHT_ERR_NOT_NESTED.  J must be odd, so that the
+ * node j = (J+1)/2 lies on the Equator. */
+int sht_plan_create_grid(int N, int J, int I, int nfields, int precision, int grid,
+                         sht_plan_t* out);
+
 /* Free a plan and its device memory (synchronises the plan's device).
  * NULL is a no-op returning SHT_OK; a destroyed handle gives SHT_ERR_HANDLE
  * as long as its memory has not been reused. */
@@ -127,7 +148,8 @@ int sht_adjoint(sht_plan_t plan, int which, const void* in, void* out,
  * latitude starting from j = 2^k (1-based) and every 2^k-th longitude,
  * read in place by strided loads (no copy).  fine_grid: device
  * [nfields][J_f][I_f] with J_f = 2^k (J+1) - 1 and I_f = 2^k I of the
- * coarse plan; 1 <= k <= 8.  Returns SHT_ERR_ARG for a bad k. */
+ * coarse plan; 1 <= k <= 8.  Returns SHT_ERR_ARG for a bad k and
+ * SHT_ERR_NOT_NESTED for a plan on the shifted grid (SHT_GRID_FEJER1). */
 int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
                         void* coarse_spec, void* stream);
 

@@ -152,8 +152,17 @@ extern "C" const char* sht_version(void) { return "cc-sht 0.1 (sm_103a)"; }
 
 extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
                                sht_plan_t* out) {
+    return sht_plan_create_grid(N, J, I, nfields, precision, SHT_GRID_CC, out);
+}
+
+extern "C" int sht_plan_create_grid(int N, int J, int I, int nfields, int precision,
+                                    int grid, sht_plan_t* out) {
     g_error.clear();
     if (!out) { set_error("out is NULL"); return SHT_ERR_ARG; }
+    if (grid != SHT_GRID_CC && grid != SHT_GRID_FEJER1) {
+        set_error("unknown latitude grid %d", grid);
+        return SHT_ERR_ARG;
+    }
     if (N < 0) { set_error("N = %d < 0", N); return SHT_ERR_ARG; }
     if (J < 1 || J % 2 == 0) {
         set_error("J = %d must be odd and >= 1 (the Equator node is needed)", J);
@@ -181,6 +190,7 @@ extern "C" int sht_plan_create(int N, int J, int I, int nfields, int precision,
 
     sht_plan_s* p = new (std::nothrow) sht_plan_s();
     if (!p) { set_error("host allocation failed"); return SHT_ERR_ALLOC; }
+    p->grid = grid;
     p->N = N; p->J = J; p->I = I; p->F = nfields; p->prec = precision;
     p->exact = (J >= 2 * N + 1) ? 1 : 0;
     p->Jh = (J + 1) / 2;
@@ -414,6 +424,10 @@ extern "C" int sht_restrict_nested(sht_plan_t p, const void* fine_grid, int k,
     int rc = check_plan(p);
     if (rc) return rc;
     if (!fine_grid || !coarse_spec) { set_error("NULL buffer"); return SHT_ERR_ARG; }
+    if (p->grid != SHT_GRID_CC) {
+        set_error("the shifted (Fejer first-rule) grid does not nest (Sec. 3.3)");
+        return SHT_ERR_NOT_NESTED;
+    }
     if (k < 1 || k > 8) { set_error("k = %d must be in 1..8", k); return SHT_ERR_ARG; }
     const long long s2 = 1LL << k;
     const long long Jf = s2 * (p->J + 1) - 1, If = s2 * p->I;

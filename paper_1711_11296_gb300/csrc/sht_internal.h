@@ -97,6 +97,7 @@ struct sht_plan_s {
     int num_sms;     // SMs of the device (grid of the persistent kernels)
     size_t ncoef;
     int ldp;         // leading dimension of the P~ table (>= Jh)
+    int grid;        // latitude grid: SHT_GRID_CC (Sec. 3) or SHT_GRID_FEJER1 (Sec. 3.3)
     int G;           // fields per FFT CTA
     int fft_threads;
     size_t fft_smem;

@@ -13,25 +13,46 @@ namespace sht {
 // w_j = 4 sin(theta_j)/(J+1) sum_{p odd <= J} sin(p theta_j)/p, each
 // sin(p theta_j) taken after the exact integer reduction of p*j modulo
 // 2(J+1).  One thread per node; O(J) work each.
-__global__ void nodes_weights_kernel(int J, int Jh, int I, double* mu,
+__global__ void nodes_weights_kernel(int J, int Jh, int I, int grid, double* mu,
                                      double* sn, double* w, double* w_over_I) {
     const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (j0 >= Jh) return;
     const int j = j0 + 1;
-    double s, c;
-    if (2 * j == J + 1) {
-        s = 1.0;
-        c = 0.0;
+    double s, c, wj;
+    if (grid == SHT_GRID_FEJER1) {
+        // Eq. (fejer1-points): theta_j = (j - 1/2) pi / J; the weights of
+        // Fejer's first rule, w_j = (2/J) (1 - 2 sum_{p=1}^{floor(J/2)}
+        // cos(2 p theta_j) / (4p^2 - 1)) (Eq. fejer1-wgt with the factor 2
+        // that makes the rule interpolatory), each cosine after reducing the
+        // integer p (2j - 1) modulo 2J
+        if (2 * j - 1 == J) {
+            s = 1.0;
+            c = 0.0;
+        } else {
+            sincospi((double)(2 * j - 1) / (double)(2 * J), &s, &c);
+        }
+        const long long period = 2LL * J;
+        double acc = 0.0;
+        for (int p = 1; p <= J / 2; ++p) {
+            const long long r = ((long long)p * (2 * j - 1)) % period;
+            acc += cospi((double)r / (double)J) / (4.0 * p * p - 1.0);
+        }
+        wj = 2.0 / (double)J * (1.0 - 2.0 * acc);
     } else {
-        sincospi((double)j / (double)(J + 1), &s, &c);
+        if (2 * j == J + 1) {
+            s = 1.0;
+            c = 0.0;
+        } else {
+            sincospi((double)j / (double)(J + 1), &s, &c);
+        }
+        const long long period = 2LL * (J + 1);
+        double acc = 0.0;
+        for (int p = 1; p <= J; p += 2) {
+            const long long r = ((long long)p * j) % period;
+            acc += sinpi((double)r / (double)(J + 1)) / (double)p;
+        }
+        wj = 4.0 * s / (double)(J + 1) * acc;
     }
-    const long long period = 2LL * (J + 1);
-    double acc = 0.0;
-    for (int p = 1; p <= J; p += 2) {
-        const long long r = ((long long)p * j) % period;
-        acc += sinpi((double)r / (double)(J + 1)) / (double)p;
-    }
-    const double wj = 4.0 * s / (double)(J + 1) * acc;
     mu[j0] = c;
     sn[j0] = s;
     w[j0] = wj;
@@ -138,7 +159,7 @@ cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s) {
 cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s) {
     const int threads = 128;
     nodes_weights_kernel<<<(p->Jh + threads - 1) / threads, threads, 0, s>>>(
-        p->J, p->Jh, p->I, p->d_mu, p->d_sin, p->d_w, p->d_w_over_I);
+        p->J, p->Jh, p->I, p->grid, p->d_mu, p->d_sin, p->d_w, p->d_w_over_I);
     return cudaGetLastError();
 }
 

@@ -17,16 +17,21 @@ def _stream_ptr(device):
 
 
 class Plan:
-    """Spherical-harmonic transform plan on the J x I Clenshaw-Curtis grid.
+    """Spherical-harmonic transform plan on the J x I Clenshaw-Curtis grid
+    (``grid="cc"``) or on the shifted grid of Fejer's first rule
+    (``grid="fejer1"``, Sec. 3.3).
 
     Layouts: grid ``[nfields, J, I]`` real; spectrum ``[ncoef, nfields]``
     complex (packed m-major, m >= 0 only).  ``precision`` is one of "fp64",
     "bf16x2", "bf16x3", "fp16x2", "fp16x3"; FP64 plans use float64/complex128
     tensors, split plans float32/complex64."""
 
-    def __init__(self, N, J, I, nfields, precision="fp64", device=None):
+    def __init__(self, N, J, I, nfields, precision="fp64", device=None, grid="cc"):
         if precision not in PRECISION:
             raise ValueError("precision must be one of %s" % list(PRECISION))
+        if grid not in _native.GRID:
+            raise ValueError("grid must be one of %s" % list(_native.GRID))
+        self.grid = grid
         self.device = torch.device("cuda", torch.cuda.current_device()
                                    if device is None else torch.device(device).index or 0)
         self.N, self.J, self.I, self.F = N, J, I, nfields
@@ -36,8 +41,8 @@ class Plan:
         self.ncoef = (N + 1) * (N + 2) // 2
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            rc = check(lib.sht_plan_create(N, J, I, nfields, PRECISION[precision],
-                                           ctypes.byref(h)))
+            rc = check(lib.sht_plan_create_grid(N, J, I, nfields, PRECISION[precision],
+                                                _native.GRID[grid], ctypes.byref(h)))
         self.exact = rc == _native.SHT_OK
         self._h = h
 
