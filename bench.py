@@ -48,6 +48,9 @@ def parse_args():
                     help="field-levels per GPU (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--reduced", action="store_true",
+                    help="split paths: the reduced transform of Sec. 4.1 "
+                         "(|P~| < 1e-16 neglected per tile)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the plan's default launch shapes")
     ap.add_argument("--no-fp64", action="store_true",
@@ -351,6 +354,8 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     import torch
     from paper_1711_11296_gb300 import sht, workloads as W
     plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid=args.grid)
+    if args.reduced and prec != "fp64":
+        plan.set_reduced(True)
     # launch shapes picked by the library's autotuner (plan setup, untimed)
     tuning = plan.tuning if args.no_autotune else plan.autotune(reps=2)
     a = W.workload_spectrum(w, F=F, field0=rank * F)
@@ -502,6 +507,7 @@ def native_arm(args):
             "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
                        "field_levels_per_gpu": F, "path": prec, "grid": args.grid,
+                       "reduced_transform": bool(args.reduced),
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch_shapes": head.get("tuning"),
                        "l2": "inputs larger than L2 (grid %.1f GB)"

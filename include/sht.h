@@ -234,6 +234,18 @@ int sht_plan_get_tuning(sht_plan_t plan, int* fields_per_cta, int* tile_width);
 int sht_plan_autotune(sht_plan_t plan, int reps, void* stream, int* fields_per_cta,
                       int* tile_width, float* ms_per_pair);
 
+/* Reduced transform (Sec. 4.1, the option of the paper's own runs): the
+ * Legendre sums neglect P~_n^m(mu_j) below 1e-16 in magnitude.  Here that is
+ * done per tile and conservatively: for each (m, parity) the nodes nearer
+ * the pole than the first node where some |P~_n^m| of that parity reaches
+ * 1e-16 are dropped in whole 16-node K tiles of the forward contraction and
+ * whole 128-node row tiles of the inverse one (those rows are written as
+ * zero).  Split plans only (SHT_ERR_UNSUPPORTED for FP64); on = 0 restores
+ * the full sums.  Synchronises the device and rebuilds the plan's problem
+ * and tile lists; groups that hold the plan keep working and follow the
+ * setting, since the set of tiles does not change. */
+int sht_plan_set_reduced(sht_plan_t plan, int on);
+
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
  * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,

@@ -18,7 +18,7 @@ EXPORTED = [
     "sht_forward_noalloc", "sht_plan_status", "sht_group_create",
     "sht_group_destroy", "sht_group_forward", "sht_group_inverse",
     "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
-    "sht_plan_create_grid",
+    "sht_plan_create_grid", "sht_plan_set_reduced",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -50,6 +50,7 @@ def _load():
     vp, ip, i = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_int
     lib.sht_plan_create.argtypes = [i, i, i, i, i, ctypes.POINTER(vp)]
     lib.sht_plan_create_grid.argtypes = [i, i, i, i, i, i, ctypes.POINTER(vp)]
+    lib.sht_plan_set_reduced.argtypes = [vp, i]
     lib.sht_plan_destroy.argtypes = [vp]
     lib.sht_plan_query.argtypes = [vp, ip, ip, ip, ip, ip, ip,
                                    ctypes.POINTER(ctypes.c_size_t)]

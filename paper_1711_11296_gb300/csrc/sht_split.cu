@@ -55,6 +55,8 @@ struct SplitProb {
     int o_stride;      // floats between output rows
     long long rs_off;  // first row of this problem in the row-scale array
     long long bt_off;  // pre-split B: byte offset of this problem's tiles in each plane
+    int kt0;           // reduced transform, forward: first K tile with |P~| >= 1e-16
+    int mt0;           // reduced transform, inverse: row tiles below mt0 are all < 1e-16
 };
 
 struct SplitTables {
@@ -70,6 +72,8 @@ struct SplitTables {
     unsigned char* inv_bplanes = nullptr;   // the spectrum split per call (inverse B)
     size_t inv_bplane_bytes = 0;
     int inv_max_nkt = 0;
+    std::vector<int> jmin;        // reduced transform: per problem, the first node
+                                  // (from the pole) with some |P~| >= 1e-16; empty: off
     SplitProb* d_probs_fwd = nullptr;
     SplitProb* d_probs_inv = nullptr;
     int4* d_tiles_fwd = nullptr;
@@ -320,7 +324,11 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SplitProb pr = g.probs[tile.x];
     const int mt = tile.y, ct = tile.z;
-    const int nkt = pr.nkt;
+    // stages it = kb .. kb + nst - 1 (the reduced transform skips the K tiles
+    // of negligible P~ in the forward direction and whole row tiles in the
+    // inverse one, whose outputs are then written as zero)
+    const int kb = pr.kt0;
+    const int nst = (mt < pr.mt0) ? 0 : pr.nkt - pr.kt0;
     const uint32_t bar0 = smem_u32(bars);
     auto full_a = [&](int s) { return bar0 + 8u * s; };
     auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
@@ -359,9 +367,10 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     if (warp == WARP_PRODUCER) {
         // ---- producer: A tiles (and pre-split B tiles), lane 0 ----
         const uint32_t abytes = (uint32_t)h * TK * 2;
-        for (int it = 0; it < nkt; ++it) {
-            const int s = it % NS;
-            const uint32_t ph = (uint32_t)(it / NS) & 1u;
+        for (int li = 0; li < nst; ++li) {
+            const int it = kb + li;
+            const int s = li % NS;
+            const uint32_t ph = (uint32_t)(li / NS) & 1u;
             bool ok = true;
             if (lane == 0) ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -393,9 +402,10 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             const int cbase = ct * TN;
             const int ccopy = min(TN, g.C - cbase);   // valid columns
             const uint32_t rbytes = (uint32_t)ccopy * 4u;
-            for (int it = 0; it < nkt; ++it) {
-                const int r = it % (NR > 0 ? NR : 1);
-                const uint32_t ph = (uint32_t)(it / (NR > 0 ? NR : 1)) & 1u;
+            for (int li = 0; li < nst; ++li) {
+                const int it = kb + li;
+                const int r = li % (NR > 0 ? NR : 1);
+                const uint32_t ph = (uint32_t)(li / (NR > 0 ? NR : 1)) & 1u;
                 bool ok = true;
                 if (lane == 0) ok = mbar_wait(empty_r(r), ph ^ 1u, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
@@ -423,9 +433,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                                         ((uint32_t)(TM >> 4) << 24);
             (void)idesc_swap;
             bool ok = true;
-            for (int it = 0; it < nkt && ok; ++it) {
-                const int s = it % NS;
-                const uint32_t ph = (uint32_t)(it / NS) & 1u;
+            for (int li = 0; li < nst && ok; ++li) {
+                const int s = li % NS;
+                const uint32_t ph = (uint32_t)(li / NS) & 1u;
                 ok = mbar_wait(full_a(s), ph, abort_flag) &&
                      (BPRE || mbar_wait(full_b(s), ph, abort_flag));
                 if (!ok) break;
@@ -447,7 +457,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                             // others, (0,1), opens the correction accumulator
                             const bool lead = (a == 0 && b == 0);
                             const uint32_t acc =
-                                (it > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
+                                (li > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
                             if constexpr (SWAP)
                                 mma_f16_rt(lead ? tmem : tmem + TN, bd, ad, idesc_swap, acc);
                             else
@@ -477,13 +487,14 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             asm volatile("bar.sync 1, %0;" ::"r"(NCONV) : "memory");
         }
         constexpr int NRS = NR > 0 ? NR : 1;
-        for (int it = 0; it < (BPRE ? 0 : nkt); ++it) {
-            const int s = it % NS, r = it % NRS;
-            const uint32_t ph = (uint32_t)(it / NS) & 1u;
+        for (int li = 0; li < (BPRE ? 0 : nst); ++li) {
+            const int it = kb + li;
+            const int s = li % NS, r = li % NRS;
+            const uint32_t ph = (uint32_t)(li / NS) & 1u;
             // the stage's B-term area is free once the MMAs of its previous
             // use are done; the FP32 rows wait in raw slot r
             if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
-            if (g.raw_bulk && !mbar_wait(full_r(r), (uint32_t)(it / NRS) & 1u, abort_flag)) break;
+            if (g.raw_bulk && !mbar_wait(full_r(r), (uint32_t)(li / NRS) & 1u, abort_flag)) break;
             unsigned char* stg = smem + s * CF::STAGE_BYTES;
             const float* raw =
                 reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
@@ -527,7 +538,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         }
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the tile
         // rows it may access) for column half w / 4 ----
-        const bool have = nkt > 0;
+        const bool have = nst > 0;
         bool ok = true;
         if (have) ok = mbar_wait(done, 0, abort_flag);
         // the TMEM loads and shuffles below are warp-collective: agree on ok
@@ -638,7 +649,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     if (warp == 0) {
         // MMAs still in flight after an abort must finish before the
         // accumulator is released (bounded as well).
-        if (*abort_flag && nkt > 0) {
+        if (*abort_flag && nst > 0) {
             const long long t0 = clock64();
             while (!mbar_try(done, 0) && clock64() - t0 < kWaitCycles) {
             }
@@ -899,9 +910,10 @@ int terms_of(int prec) { return (prec == SHT_BF16X2 || prec == SHT_FP16X2) ? 2 :
 
 // Problems (one per (m, parity)) and tiles of both directions for
 // truncation N, Jh northern nodes and C real columns; tile.w = plan.
-void build_split_lists(int N, int Jh, int C, int tn, int plan, std::vector<SplitProb>& pf,
-                       std::vector<SplitProb>& pi, std::vector<int4>& tf,
-                       std::vector<int4>& ti, long long& fwd_bytes, long long& inv_bytes) {
+void build_split_lists(int N, int Jh, int C, int tn, int plan, const std::vector<int>& jmin,
+                       std::vector<SplitProb>& pf, std::vector<SplitProb>& pi,
+                       std::vector<int4>& tf, std::vector<int4>& ti, long long& fwd_bytes,
+                       long long& inv_bytes) {
     const int nprob = 2 * (N + 1);
     pf.assign(nprob, SplitProb{});
     pi.assign(nprob, SplitProb{});
@@ -921,6 +933,12 @@ void build_split_lists(int N, int Jh, int C, int tn, int plan, std::vector<Split
             f.Mrows = R;
             f.K = Jh;
             f.nkt = (Jh + TK - 1) / TK;
+            // reduced transform: K tiles entirely nearer the pole than the
+            // first significant node are skipped; inverse row tiles entirely
+            // there are written as zero
+            const int j0 = jmin.empty() ? 0 : jmin[2 * m + q];
+            f.kt0 = std::min(j0 / TK, f.nkt);
+            f.mt0 = 0;
             f.b_off = (long long)(2 * m + q) * Jh * C;
             f.b_stride = C;
             f.o_off = row0 * C;
@@ -938,6 +956,8 @@ void build_split_lists(int N, int Jh, int C, int tn, int plan, std::vector<Split
             v.Mrows = Jh - 1;
             v.K = R;
             v.nkt = (R + TK - 1) / TK;
+            v.kt0 = 0;
+            v.mt0 = j0 / TM;
             v.b_off = row0 * C;
             v.b_stride = 2 * C;
             v.o_off = (long long)(2 * m + q) * Jh * C;
@@ -1058,7 +1078,7 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
     std::vector<SplitProb> pf, pi;
     std::vector<int4> tf, ti;
     long long fwd_bytes = 0, inv_bytes = 0;
-    build_split_lists(N, Jh, C, TN_MAX, 0, pf, pi, tf, ti, fwd_bytes, inv_bytes);
+    build_split_lists(N, Jh, C, TN_MAX, 0, st->jmin, pf, pi, tf, ti, fwd_bytes, inv_bytes);
     st->fwd_plane_bytes = (size_t)(fwd_bytes + 255) / 256 * 256;
     st->inv_plane_bytes = (size_t)(inv_bytes + 255) / 256 * 256;
     st->ntiles_fwd = (int)tf.size();
@@ -1142,18 +1162,17 @@ void split_tables_destroy(sht_plan_s* p) {
     p->d_colmax = nullptr;
 }
 
-// Rebuild the tile lists of a split plan for column tiles TN = tn (64 or
-// 128).  The term planes and row scales do not depend on the width; the
-// pre-split spectrum planes were sized for the widest tiles.  Synchronises
-// the device: kernels in flight may still read the old lists.
-cudaError_t split_set_tile_width(sht_plan_s* p, int tn) {
+// Rebuild the problem and tile lists of a split plan for column tiles
+// TN = tn (64 or 128) and the reduced-transform ranges st->jmin.  The term
+// planes and row scales depend on neither; the pre-split spectrum planes
+// were sized for the widest tiles.  Synchronises the device: kernels in
+// flight may still read the old lists.
+cudaError_t split_rebuild_lists(sht_plan_s* p, int tn) {
     SplitTables* st = p->split;
-    if (!st || (tn != 64 && tn != 128)) return cudaErrorInvalidValue;
-    if (st->tn == tn) return cudaSuccess;
     std::vector<SplitProb> pf, pi;
     std::vector<int4> tf, ti;
     long long fb = 0, ib = 0;
-    build_split_lists(p->N, p->Jh, 2 * p->F, tn, 0, pf, pi, tf, ti, fb, ib);
+    build_split_lists(p->N, p->Jh, 2 * p->F, tn, 0, st->jmin, pf, pi, tf, ti, fb, ib);
     int4 *dtf = nullptr, *dti = nullptr;
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMalloc(&dtf, (tf.size() + 1) * sizeof(int4));
@@ -1162,6 +1181,9 @@ cudaError_t split_set_tile_width(sht_plan_s* p, int tn) {
         e = cudaMemcpy(dtf, tf.data(), tf.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(dti, ti.data(), ti.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(st->d_probs_fwd, pf.data(), pf.size() * sizeof(SplitProb),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(st->d_probs_inv, pi.data(), pi.size() * sizeof(SplitProb),
                        cudaMemcpyHostToDevice);
@@ -1180,6 +1202,61 @@ cudaError_t split_set_tile_width(sht_plan_s* p, int tn) {
     return cudaSuccess;
 }
 
+cudaError_t split_set_tile_width(sht_plan_s* p, int tn) {
+    SplitTables* st = p->split;
+    if (!st || (tn != 64 && tn != 128)) return cudaErrorInvalidValue;
+    if (st->tn == tn) return cudaSuccess;
+    return split_rebuild_lists(p, tn);
+}
+
+namespace {
+// First northern node (0 = nearest the pole) at which some P~_n^m of the
+// problem's parity reaches thr in magnitude; Jh if none.  One block per
+// (m, parity) problem, threads over the nodes.
+__global__ void jmin_kernel(const double* __restrict__ pnm, int ldp, int N, int Jh, double thr,
+                            int* out) {
+    __shared__ int first;
+    const int p = blockIdx.x, m = p >> 1, q = p & 1;
+    if (threadIdx.x == 0) first = Jh;
+    __syncthreads();
+    const size_t row0 = coef_offset(N, m) + q;
+    const int d = N - m - q;
+    const int R = d >= 0 ? d / 2 + 1 : 0;
+    for (int j = threadIdx.x; j < Jh; j += blockDim.x) {
+        bool sig = false;
+        for (int r = 0; r < R && !sig; ++r) sig = fabs(pnm[(row0 + 2 * (size_t)r) * ldp + j]) >= thr;
+        if (sig) atomicMin(&first, j);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) out[p] = first;
+}
+}  // namespace
+
+// Reduced transform (Sec. 4.1: terms with |P~| < 1e-16 neglected, as in the
+// paper's own runs), for split plans: on = 1 finds the per-problem ranges
+// and rebuilds the lists, on = 0 restores the full transform.
+cudaError_t split_set_reduced(sht_plan_s* p, int on) {
+    SplitTables* st = p->split;
+    if (!st) return cudaErrorInvalidValue;
+    if ((on != 0) == !st->jmin.empty()) return cudaSuccess;
+    const int nprob = 2 * (p->N + 1);
+    if (on) {
+        int* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, nprob * sizeof(int));
+        if (e != cudaSuccess) return e;
+        jmin_kernel<<<nprob, 256>>>(p->d_pnm, p->ldp, p->N, p->Jh, 1e-16, d);
+        e = cudaGetLastError();
+        std::vector<int> h(nprob);
+        if (e == cudaSuccess) e = cudaMemcpy(h.data(), d, nprob * sizeof(int), cudaMemcpyDeviceToHost);
+        cudaFree(d);
+        if (e != cudaSuccess) return e;
+        st->jmin = h;
+    } else {
+        st->jmin.clear();
+    }
+    return split_rebuild_lists(p, st->tn);
+}
+
 int split_tile_width(const sht_plan_s* p) { return p->split ? p->split->tn : 0; }
 
 // Tiles of a group of split plans (same term count), heaviest first: every
@@ -1191,9 +1268,13 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
         std::vector<SplitProb> pf, pi;
         std::vector<int4> tf, ti;
         long long fb, ib;
-        build_split_lists(p->N, p->Jh, 2 * p->F, p->split->tn, q, pf, pi, tf, ti, fb, ib);
+        build_split_lists(p->N, p->Jh, 2 * p->F, p->split->tn, q, p->split->jmin, pf, pi, tf,
+                          ti, fb, ib);
         const std::vector<SplitProb>& pr = inverse ? pi : pf;
-        for (const int4& t : inverse ? ti : tf) all.push_back({pr[t.x].nkt, t});
+        for (const int4& t : inverse ? ti : tf) {
+            const SplitProb& v = pr[t.x];
+            all.push_back({t.y < v.mt0 ? 0 : v.nkt - v.kt0, t});
+        }
     }
     std::stable_sort(all.begin(), all.end(),
                      [](const std::pair<int, int4>& a, const std::pair<int, int4>& b) {

@@ -23,6 +23,7 @@ namespace sht {
 
 cudaError_t split_set_tile_width(sht_plan_s* p, int tn);
 int split_tile_width(const sht_plan_s* p);
+cudaError_t split_set_reduced(sht_plan_s* p, int on);
 
 namespace {
 
@@ -211,5 +212,23 @@ extern "C" int sht_plan_autotune(sht_plan_t p, int reps, void* stream, int* fiel
     if (fields_per_cta) *fields_per_cta = best.G;
     if (tile_width) *tile_width = fp64 ? 0 : best.tn;
     if (ms_per_pair) *ms_per_pair = best.ms;
+    return SHT_OK;
+}
+
+extern "C" int sht_plan_set_reduced(sht_plan_t p, int on) {
+    if (!p || !plan_is_live(p)) {
+        set_error("invalid or destroyed plan handle");
+        return SHT_ERR_HANDLE;
+    }
+    if (p->prec == SHT_FP64) {
+        set_error("the reduced transform is available for split plans");
+        return SHT_ERR_UNSUPPORTED;
+    }
+    DeviceGuard dg(p->device);
+    const cudaError_t e = split_set_reduced(p, on ? 1 : 0);
+    if (e != cudaSuccess) {
+        set_error("reduced transform: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SHT_ERR_ALLOC : SHT_ERR_CUDA;
+    }
     return SHT_OK;
 }

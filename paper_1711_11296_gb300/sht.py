@@ -145,6 +145,12 @@ class Plan:
         with torch.cuda.device(self.device):
             check(lib.sht_plan_set_tuning(self._h, int(fields_per_cta), int(tile_width)))
 
+    def set_reduced(self, on=True):
+        """Reduced transform (Sec. 4.1): neglect |P~| < 1e-16, per tile
+        (split plans only)."""
+        with torch.cuda.device(self.device):
+            check(lib.sht_plan_set_reduced(self._h, 1 if on else 0))
+
     def autotune(self, reps=3):
         """Time the candidate launch shapes on this plan and keep the fastest;
         returns the choice and the mean ms of an inverse + forward pair."""
