@@ -240,8 +240,9 @@ int sht_plan_autotune(sht_plan_t plan, int reps, void* stream, int* fields_per_c
  * the pole than the first node where some |P~_n^m| of that parity reaches
  * 1e-16 are dropped in whole 16-node K tiles of the forward contraction and
  * whole 128-node row tiles of the inverse one (those rows are written as
- * zero).  Split plans only (SHT_ERR_UNSUPPORTED for FP64); on = 0 restores
- * the full sums.  Synchronises the device and rebuilds the plan's problem
+ * zero).  FP64 plans drop whole 16-node K chunks of the forward sums and
+ * whole 32-node row tiles of the inverse ones the same way.  on = 0
+ * restores the full sums.  Synchronises the device and rebuilds the plan's problem
  * and tile lists; groups that hold the plan keep working and follow the
  * setting, since the set of tiles does not change. */
 int sht_plan_set_reduced(sht_plan_t plan, int on);

@@ -124,6 +124,8 @@ struct sht_plan_s {
 
     int* d_status;             // device status word: kernels OR in failure bits
                                // (1: tensor-core wait timed out, 2: FFT wait timed out)
+    int* d_jmin;               // FP64 plans with the reduced transform: [2(N+1)]
+                               // first node with some |P~| >= 1e-16 (null: off)
     sht::SplitTables* split;   // null for FP64 plans
     unsigned* d_colmax;        // FP16 split plans: [2][2F] column maxima (float bits)
                                // of the forward and inverse GEMMs' FP32 operand

@@ -31,9 +31,12 @@ __device__ __forceinline__ size_t dcoef_offset(int N, int m) {
     return (size_t)m * (N + 1) - (size_t)m * (m - 1) / 2;
 }
 
+// jmin (may be null): reduced transform (Sec. 4.1), per (m, parity) the
+// first node with some |P~| >= 1e-16; the forward K loop starts at its
+// K chunk, and inverse row tiles wholly before it are written as zero.
 __device__ __forceinline__ void legendre_fwd_body(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ work,
-    double* __restrict__ spec, int4 t, int N, int Jh, int C) {
+    double* __restrict__ spec, int4 t, int N, int Jh, int C, const int* __restrict__ jmin) {
     __shared__ double Ps[BK][BM + 1];
     __shared__ double Bs[BK][BN];
     const int m = t.x, q = t.y & 1, r0 = t.z, c0 = t.w;
@@ -42,7 +45,8 @@ __device__ __forceinline__ void legendre_fwd_body(
     const double* B = work + ((size_t)(2 * m + q) * Jh) * C;
     const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
     double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int k0 = 0; k0 < Jh; k0 += BK) {
+    const int kstart = jmin ? (jmin[2 * m + q] / BK) * BK : 0;
+    for (int k0 = kstart; k0 < Jh; k0 += BK) {
 #pragma unroll
         for (int u = 0; u < (BM * BK) / NT; ++u) {
             const int e = tid + u * NT;
@@ -85,7 +89,7 @@ __device__ __forceinline__ void legendre_fwd_body(
 
 __device__ __forceinline__ void legendre_inv_body(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ spec,
-    double* __restrict__ work, int4 t, int N, int Jh, int C) {
+    double* __restrict__ work, int4 t, int N, int Jh, int C, const int* __restrict__ jmin) {
     __shared__ double Ps[BK][BM];
     __shared__ double Bs[BK][BN];
     const int m = t.x, q = t.y & 1, j0 = t.z, c0 = t.w;
@@ -93,7 +97,9 @@ __device__ __forceinline__ void legendre_inv_body(
     const size_t row0 = dcoef_offset(N, m) + q;
     const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
     double acc[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int k0 = 0; k0 < R; k0 += BK) {
+    // (block-uniform: the loop holds barriers)
+    const int kend = (jmin && j0 + BM <= jmin[2 * m + q]) ? 0 : R;
+    for (int k0 = 0; k0 < kend; k0 += BK) {
 #pragma unroll
         for (int u = 0; u < (BM * BK) / NT; ++u) {
             const int e = tid + u * NT;
@@ -136,14 +142,16 @@ __device__ __forceinline__ void legendre_inv_body(
 
 __global__ void __launch_bounds__(NT) legendre_fwd_fp64_kernel(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ work,
-    double* __restrict__ spec, const int4* __restrict__ tiles, int N, int Jh, int C) {
-    legendre_fwd_body(pnm, ldp, work, spec, tiles[blockIdx.x], N, Jh, C);
+    double* __restrict__ spec, const int4* __restrict__ tiles, int N, int Jh, int C,
+    const int* __restrict__ jmin) {
+    legendre_fwd_body(pnm, ldp, work, spec, tiles[blockIdx.x], N, Jh, C, jmin);
 }
 
 __global__ void __launch_bounds__(NT) legendre_inv_fp64_kernel(
     const double* __restrict__ pnm, int ldp, const double* __restrict__ spec,
-    double* __restrict__ work, const int4* __restrict__ tiles, int N, int Jh, int C) {
-    legendre_inv_body(pnm, ldp, spec, work, tiles[blockIdx.x], N, Jh, C);
+    double* __restrict__ work, const int4* __restrict__ tiles, int N, int Jh, int C,
+    const int* __restrict__ jmin) {
+    legendre_inv_body(pnm, ldp, spec, work, tiles[blockIdx.x], N, Jh, C, jmin);
 }
 
 // Grouped launches: tile.y = parity + 2 * (plan index in the group).
@@ -153,20 +161,23 @@ struct LegGroup {
     const double* in[kMaxGroup];
     double* out[kMaxGroup];
     int ldp[kMaxGroup], N[kMaxGroup], Jh[kMaxGroup], C[kMaxGroup];
+    const int* jmin[kMaxGroup];
 };
 
 __global__ void __launch_bounds__(NT) legendre_fwd_fp64_group_kernel(
     const __grid_constant__ LegGroup G, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
     const int p = t.y >> 1;
-    legendre_fwd_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p]);
+    legendre_fwd_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p],
+                      G.jmin[p]);
 }
 
 __global__ void __launch_bounds__(NT) legendre_inv_fp64_group_kernel(
     const __grid_constant__ LegGroup G, const int4* __restrict__ tiles) {
     const int4 t = tiles[blockIdx.x];
     const int p = t.y >> 1;
-    legendre_inv_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p]);
+    legendre_inv_body(G.pnm[p], G.ldp[p], G.in[p], G.out[p], t, G.N[p], G.Jh[p], G.C[p],
+                      G.jmin[p]);
 }
 
 }  // namespace
@@ -184,6 +195,7 @@ cudaError_t launch_legendre_fp64_group(sht_plan_s* const* plans, int n, bool inv
         G.C[q] = 2 * plans[q]->F;
         G.in[q] = static_cast<const double*>(in[q]);
         G.out[q] = static_cast<double*>(out[q]);
+        G.jmin[q] = plans[q]->d_jmin;
     }
     if (ntiles == 0) return cudaSuccess;
     if (inverse)
@@ -216,7 +228,7 @@ cudaError_t launch_legendre_fwd_fp64(const sht_plan_s* p, const double* work,
                                      double* spec, cudaStream_t s) {
     if (p->ntiles_fwd == 0) return cudaSuccess;
     legendre_fwd_fp64_kernel<<<p->ntiles_fwd, NT, 0, s>>>(
-        p->d_pnm, p->ldp, work, spec, p->d_tiles_fwd, p->N, p->Jh, 2 * p->F);
+        p->d_pnm, p->ldp, work, spec, p->d_tiles_fwd, p->N, p->Jh, 2 * p->F, p->d_jmin);
     return cudaGetLastError();
 }
 
@@ -224,7 +236,7 @@ cudaError_t launch_legendre_inv_fp64(const sht_plan_s* p, const double* spec,
                                      double* work, cudaStream_t s) {
     if (p->ntiles_inv == 0) return cudaSuccess;
     legendre_inv_fp64_kernel<<<p->ntiles_inv, NT, 0, s>>>(
-        p->d_pnm, p->ldp, spec, work, p->d_tiles_inv, p->N, p->Jh, 2 * p->F);
+        p->d_pnm, p->ldp, spec, work, p->d_tiles_inv, p->N, p->Jh, 2 * p->F, p->d_jmin);
     return cudaGetLastError();
 }
 

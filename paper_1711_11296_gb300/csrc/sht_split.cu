@@ -1232,6 +1232,12 @@ __global__ void jmin_kernel(const double* __restrict__ pnm, int ldp, int N, int 
 }
 }  // namespace
 
+// jmin for every (m, parity) problem of the plan into d_out[2(N+1)].
+cudaError_t launch_jmin(const sht_plan_s* p, int* d_out, cudaStream_t s) {
+    jmin_kernel<<<2 * (p->N + 1), 256, 0, s>>>(p->d_pnm, p->ldp, p->N, p->Jh, 1e-16, d_out);
+    return cudaGetLastError();
+}
+
 // Reduced transform (Sec. 4.1: terms with |P~| < 1e-16 neglected, as in the
 // paper's own runs), for split plans: on = 1 finds the per-problem ranges
 // and rebuilds the lists, on = 0 restores the full transform.
@@ -1244,8 +1250,7 @@ cudaError_t split_set_reduced(sht_plan_s* p, int on) {
         int* d = nullptr;
         cudaError_t e = cudaMalloc(&d, nprob * sizeof(int));
         if (e != cudaSuccess) return e;
-        jmin_kernel<<<nprob, 256>>>(p->d_pnm, p->ldp, p->N, p->Jh, 1e-16, d);
-        e = cudaGetLastError();
+        e = launch_jmin(p, d, nullptr);
         std::vector<int> h(nprob);
         if (e == cudaSuccess) e = cudaMemcpy(h.data(), d, nprob * sizeof(int), cudaMemcpyDeviceToHost);
         cudaFree(d);

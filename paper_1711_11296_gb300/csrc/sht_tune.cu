@@ -24,6 +24,7 @@ namespace sht {
 cudaError_t split_set_tile_width(sht_plan_s* p, int tn);
 int split_tile_width(const sht_plan_s* p);
 cudaError_t split_set_reduced(sht_plan_s* p, int on);
+cudaError_t launch_jmin(const sht_plan_s* p, int* d_out, cudaStream_t s);
 
 namespace {
 
@@ -220,12 +221,27 @@ extern "C" int sht_plan_set_reduced(sht_plan_t p, int on) {
         set_error("invalid or destroyed plan handle");
         return SHT_ERR_HANDLE;
     }
-    if (p->prec == SHT_FP64) {
-        set_error("the reduced transform is available for split plans");
-        return SHT_ERR_UNSUPPORTED;
-    }
     DeviceGuard dg(p->device);
-    const cudaError_t e = split_set_reduced(p, on ? 1 : 0);
+    cudaError_t e = cudaSuccess;
+    if (p->prec == SHT_FP64) {
+        // the FP64 kernels read the per-problem first node from the device
+        if (on && !p->d_jmin) {
+            int* d = nullptr;
+            e = cudaMalloc(&d, 2 * (size_t)(p->N + 1) * sizeof(int));
+            if (e == cudaSuccess) e = launch_jmin(p, d, nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e == cudaSuccess)
+                p->d_jmin = d;
+            else if (d)
+                cudaFree(d);
+        } else if (!on && p->d_jmin) {
+            e = cudaDeviceSynchronize();
+            cudaFree(p->d_jmin);
+            p->d_jmin = nullptr;
+        }
+    } else {
+        e = split_set_reduced(p, on ? 1 : 0);
+    }
     if (e != cudaSuccess) {
         set_error("reduced transform: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? SHT_ERR_ALLOC : SHT_ERR_CUDA;

@@ -146,8 +146,7 @@ class Plan:
             check(lib.sht_plan_set_tuning(self._h, int(fields_per_cta), int(tile_width)))
 
     def set_reduced(self, on=True):
-        """Reduced transform (Sec. 4.1): neglect |P~| < 1e-16, per tile
-        (split plans only)."""
+        """Reduced transform (Sec. 4.1): neglect |P~| < 1e-16, per tile."""
         with torch.cuda.device(self.device):
             check(lib.sht_plan_set_reduced(self._h, 1 if on else 0))
 

@@ -45,7 +45,7 @@ def test_reduced_matches_full_and_oracle(sht, prec, N, J, I, F):
     full.status()
 
 
-def test_reduced_in_a_group_and_rejected_for_fp64(sht):
+def test_reduced_in_a_group(sht):
     cfg = [(63, 129, 256, 3), (127, 257, 512, 2)]
     plans = [sht.Plan(N, J, I, F, "bf16x3") for N, J, I, F in cfg]
     for p in plans:
@@ -57,6 +57,22 @@ def test_reduced_in_a_group_and_rejected_for_fp64(sht):
     outs = grp.inverse(specs)
     for p, a, g in zip(plans, specs, outs):
         assert torch.equal(g, p.inverse(a))
-    d = sht.Plan(15, 31, 32, 1, "fp64")
-    with pytest.raises(sht.SHTError):
-        d.set_reduced(True)
+
+
+@pytest.mark.parametrize("N,J,I,F", [(63, 129, 256, 3), (319, 641, 1280, 2)])
+def test_fp64_reduced_matches_full_and_oracle(sht, N, J, I, F):
+    full = sht.Plan(N, J, I, F, "fp64")
+    red = sht.Plan(N, J, I, F, "fp64")
+    red.set_reduced(True)
+    x = to_cuda(W.random_grid(F, J, I, seed=1620 + N), torch.float64)
+    a = to_cuda(W.random_spectrum(N, F, "energy^-2", seed=1621 + N), torch.complex128)
+    s_full, s_red = full.forward(x).cpu().numpy(), red.forward(x).cpu().numpy()
+    g_full, g_red = full.inverse(a).cpu().numpy(), red.inverse(a).cpu().numpy()
+    # the neglected terms are below 1e-16 of P~'s scale: FP64 rounding level
+    assert rel_l2(s_red, s_full) < 1e-14
+    assert rel_l2(g_red, g_full) < 1e-14
+    if N <= 63:
+        assert rel_l2(s_red, O.analysis(x.cpu().numpy(), N)) < 1e-12
+    red.set_reduced(False)
+    assert np.array_equal(red.forward(x).cpu().numpy(), s_full)
+    red.status()
