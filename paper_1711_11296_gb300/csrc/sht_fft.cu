@@ -439,7 +439,15 @@ struct InvArgs {
     FftShape shape;
 };
 
-// Copy the per-pass twiddle tables into shared memory.
+// Copy the per-pass twiddle tables into shared memory asynchronously, so
+// that they are in flight together with the CTA's data copies (one wait).
+template <typename V>
+__device__ __forceinline__ void load_twiddles_async(V* dst, const V* src, int n) {
+    for (int e = threadIdx.x; e < n; e += NT) cp_async<sizeof(V)>(dst + e, src + e);
+}
+
+// The same by plain loads and stores (measured faster ahead of the inverse
+// kernel's gathered copies).
 template <typename V>
 __device__ __forceinline__ void load_twiddles(V* dst, const V* src, int n) {
     for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
@@ -505,7 +513,6 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
                (long long)j * A.src.row_stride;
     };
 
-    load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     {
         // element k of row r goes to rows[r LP + ph(k)], copied
         // asynchronously so that all of the CTA's loads are in flight
@@ -522,6 +529,8 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
                 }
             }
         }
+        load_twiddles_async(tws, A.twp,
+                            LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
         cp_async_wait_all();
     }
     __syncthreads();
