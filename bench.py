@@ -84,6 +84,13 @@ def barrier(dist, device=None):
             dist.barrier()
 
 
+def job_throughput(world, fields_per_rank, steps, ms):
+    """Whole-job field-level pairs per second: every rank transforms its own
+    fields_per_rank field-levels per step (replicas, weak scaling), and the
+    job's time is the slowest rank's."""
+    return world * fields_per_rank * steps / (ms / 1000.0)
+
+
 def max_over_ranks(dist, value, device):
     if dist is None:
         return value
@@ -443,7 +450,7 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(dist, ev0.elapsed_time(ev1), device)
         nbytes = host_in[0].numel() * host_in[0].element_size()
-        res["e2e"] = {"value": world * F * args.steps / (e2e_ms / 1000.0),
+        res["e2e"] = {"value": job_throughput(world, F, args.steps, e2e_ms),
                       "unit": UNIT, "h2d_bytes_per_step": nbytes,
                       "d2h_bytes_per_step": nbytes,
                       "copies": "pinned host buffers, double-buffered on copy streams "
@@ -469,7 +476,7 @@ def native_arm(args):
 
     head = run_path(args, w, F, prec, device, dist, local, rank, world,
                     not args.no_e2e)
-    value = world * F * args.steps / (head["ms"] / 1000.0)
+    value = job_throughput(world, F, args.steps, head["ms"])
     prof = head["prof"]
     name, (tot_ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
     roof = roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src)
@@ -485,7 +492,7 @@ def native_arm(args):
         r64 = run_path(a64, w, F, "fp64", device, dist, local, rank, world, False)
         n64, (t64, c64) = max(r64["prof"].items(), key=lambda kv: kv[1][0])
         other = {"path": "fp64", "steps": a64.steps,
-                 "value": world * F * a64.steps / (r64["ms"] / 1000.0),
+                 "value": job_throughput(world, F, a64.steps, r64["ms"]),
                  "ms_per_step": r64["ms"] / a64.steps,
                  "roofline": roofline_for(n64, t64, c64, w, F, "fp64", pk, pk_src),
                  "gpu_launches": r64["launches"]}
