@@ -392,6 +392,9 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     plan.profile(False)
     prof = plan.profile_read()
     plan.status()
+    # NaN/Inf guard: a step that produced non-finite output is not a result
+    if not bool(torch.isfinite(torch.view_as_real(spec_out)).all()):
+        raise RuntimeError("the transform pair produced non-finite values")
     ms_local = ev0.elapsed_time(ev1)
     barrier(dist, local)
     ms = max_over_ranks(dist, ms_local, device)

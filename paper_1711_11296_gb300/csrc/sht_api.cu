@@ -4,6 +4,7 @@
 // sht_plan_copy_tables and error reporting.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <map>
 #include <mutex>
@@ -220,8 +221,13 @@ extern "C" int sht_plan_create_grid(int N, int J, int I, int nfields, int precis
 
     cudaStream_t s = nullptr;
     int rc = SHT_OK;
+    // failure-detection tests: SHT_INJECT_ALLOC_FAIL=k fails the k-th device
+    // allocation of the plan's tables as if the device were out of memory
+    int inject_alloc = 0, nalloc = 0;
+    if (const char* v = getenv("SHT_INJECT_ALLOC_FAIL")) inject_alloc = atoi(v);
     auto alloc = [&](void** ptr, size_t bytes, const char* what) -> bool {
-        e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+        e = (++nalloc == inject_alloc) ? cudaErrorMemoryAllocation
+                                       : cudaMalloc(ptr, bytes > 0 ? bytes : 16);
         if (e != cudaSuccess) {
             *ptr = nullptr;
             cudaGetLastError();

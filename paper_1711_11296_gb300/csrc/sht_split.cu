@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "sht_internal.h"
@@ -72,6 +73,7 @@ struct SplitTables {
     unsigned char* inv_bplanes = nullptr;   // the spectrum split per call (inverse B)
     size_t inv_bplane_bytes = 0;
     int inv_max_nkt = 0;
+    int inject_stall = 0;         // SHT_INJECT_STALL at plan creation (tests only)
     std::vector<int> jmin;        // reduced transform: per problem, the first node
                                   // (from the pole) with some |P~| >= 1e-16; empty: off
     SplitProb* d_probs_fwd = nullptr;
@@ -140,6 +142,7 @@ struct GemmArgs {
     const unsigned char* bplanes;   // pre-split B: term t plane at bplanes + t * bplane_bytes
     long long bplane_bytes;
     int nct;                        // column tiles (pre-split B tile index = it * nct + ct)
+    int stall;                      // fault injection for tests: CTA 0 never arms stage 0
 };
 
 // FP16 operands are scaled by powers of two into [-1, 1): column c of B by
@@ -367,6 +370,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     if (warp == WARP_PRODUCER) {
         // ---- producer: A tiles (and pre-split B tiles), lane 0 ----
         const uint32_t abytes = (uint32_t)h * TK * 2;
+        int issued = 0;
+        const bool stall = g.stall && blockIdx.x == 0;   // injected: stage 0 never armed
         for (int li = 0; li < nst; ++li) {
             const int it = kb + li;
             const int s = li % NS;
@@ -375,6 +380,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             if (lane == 0) ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
+            issued = li + 1;
+            if (stall && li == 0) continue;
             unsigned char* st = smem + s * CF::STAGE_BYTES;
             if (lane == 0) {
                 mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES) : 0u));
@@ -395,6 +402,17 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             }
             __syncwarp();
         }
+        // after an abort, let the copies already issued land before the CTA
+        // releases its shared memory (bounded; a stage never armed is skipped)
+        if (lane == 0 && *abort_flag) {
+            for (int j = max(0, issued - NS); j < issued; ++j) {
+                if (stall && j == 0) continue;
+                const long long t0 = clock64();
+                while (!mbar_try(full_a(j % NS), (uint32_t)(j / NS) & 1u) &&
+                       clock64() - t0 < kWaitCycles) {
+                }
+            }
+        }
     } else if (warp == WARP_RAW) {
         // ---- the FP32 rows of B (lane k copies row k of a stage) into the
         // raw ring, NR stages ahead of the converters ----
@@ -402,14 +420,17 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             const int cbase = ct * TN;
             const int ccopy = min(TN, g.C - cbase);   // valid columns
             const uint32_t rbytes = (uint32_t)ccopy * 4u;
+            constexpr int NRS = NR > 0 ? NR : 1;
+            int issued = 0;
             for (int li = 0; li < nst; ++li) {
                 const int it = kb + li;
-                const int r = li % (NR > 0 ? NR : 1);
-                const uint32_t ph = (uint32_t)(li / (NR > 0 ? NR : 1)) & 1u;
+                const int r = li % NRS;
+                const uint32_t ph = (uint32_t)(li / NRS) & 1u;
                 bool ok = true;
                 if (lane == 0) ok = mbar_wait(empty_r(r), ph ^ 1u, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
+                issued = li + 1;
                 const int k0 = it * TK;
                 const int krows = max(0, min(TK, pr.K - k0));
                 if (lane == 0) mbar_expect_tx(full_r(r), rbytes * (uint32_t)krows);
@@ -421,6 +442,15 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                              src, rbytes, full_r(r));
                 }
                 __syncwarp();
+            }
+            // after an abort, let the row copies already issued land (bounded)
+            if (lane == 0 && *abort_flag) {
+                for (int j = max(0, issued - NRS); j < issued; ++j) {
+                    const long long t0 = clock64();
+                    while (!mbar_try(full_r(j % NRS), (uint32_t)(j / NRS) & 1u) &&
+                           clock64() - t0 < kWaitCycles) {
+                    }
+                }
             }
         }
     } else if (warp == WARP_MMA) {
@@ -991,6 +1021,7 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.colmax = p->d_colmax ? p->d_colmax + (inverse ? g.C : 0) : nullptr;
     g.nct = (g.C + st->tn - 1) / st->tn;
     g.bplanes = inverse ? st->inv_bplanes : nullptr;
+    g.stall = (!inverse && st->inject_stall) ? 1 : 0;
     g.bplane_bytes = inverse ? (long long)st->inv_bplane_bytes : 0;
     return g;
 }
@@ -1073,6 +1104,13 @@ cudaError_t split_tables_create(sht_plan_s* p, cudaStream_t s) {
     p->split = st;
     st->terms = terms_of(p->prec);
     st->fp16 = p->prec == SHT_FP16X2 || p->prec == SHT_FP16X3;
+    // failure-detection tests: the forward GEMM's first CTA never arms its
+    // first stage, so its bounded waits run out and the plan's status word
+    // records SHT_ERR_TIMEOUT (no fault, no hang)
+    {
+        const char* v = getenv("SHT_INJECT_STALL");
+        st->inject_stall = (v && v[0] == '1') ? 1 : 0;
+    }
     const int N = p->N, Jh = p->Jh, C = 2 * p->F;
     const int nprob = 2 * (N + 1);
     std::vector<SplitProb> pf, pi;
