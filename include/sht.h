@@ -153,6 +153,24 @@ int sht_adjoint(sht_plan_t plan, int which, const void* in, void* out,
 int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
                         void* coarse_spec, void* stream);
 
+/* Multigrid prolongation in spectral space (Appendix C): the lower-
+ * resolution spectral space is a subset of this plan's, so a spectrum
+ * truncated at Nc (0 <= Nc <= N; device [ncoef(Nc)][nfields] in the
+ * spectrum layout and precision of the plan) is zero-padded to N and
+ * synthesised on this plan's grid (device [nfields][J][I]), as
+ * sht_inverse.  The first call allocates a spectrum-sized buffer that the
+ * plan keeps (SHT_ERR_ALLOC if it cannot). */
+int sht_prolong_spectral(sht_plan_t fine, const void* coarse_spec, int Nc, void* fine_grid,
+                         void* stream);
+
+/* Multigrid restriction in grid space by injection (Appendix C): the coarse
+ * plan's grid is every 2^k-th latitude (j_f = 2^k (j+1) - 1, 0-based) and
+ * every 2^k-th longitude of the fine grid [nfields][2^k (J+1) - 1][2^k I]
+ * (Sec. 3.2 nesting).  Plain strided copy; coarse_grid is [nfields][J][I].
+ * SHT_ERR_NOT_NESTED on the shifted grid, SHT_ERR_ARG for k outside 1..8. */
+int sht_inject_nested(sht_plan_t coarse, const void* fine_grid, int k, void* coarse_grid,
+                      void* stream);
+
 /* Allocation-free FP64 analysis, for callers that cannot allocate device
  * memory (no counterpart in the paper, which has no notion of memory
  * management): for example a plug-in inside an application that owns all

@@ -18,7 +18,8 @@ EXPORTED = [
     "sht_forward_noalloc", "sht_plan_status", "sht_group_create",
     "sht_group_destroy", "sht_group_forward", "sht_group_inverse",
     "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
-    "sht_plan_create_grid", "sht_plan_set_reduced",
+    "sht_plan_create_grid", "sht_plan_set_reduced", "sht_prolong_spectral",
+    "sht_inject_nested",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -51,6 +52,8 @@ def _load():
     lib.sht_plan_create.argtypes = [i, i, i, i, i, ctypes.POINTER(vp)]
     lib.sht_plan_create_grid.argtypes = [i, i, i, i, i, i, ctypes.POINTER(vp)]
     lib.sht_plan_set_reduced.argtypes = [vp, i]
+    lib.sht_prolong_spectral.argtypes = [vp, vp, i, vp, vp]
+    lib.sht_inject_nested.argtypes = [vp, vp, i, vp, vp]
     lib.sht_plan_destroy.argtypes = [vp]
     lib.sht_plan_query.argtypes = [vp, ip, ip, ip, ip, ip, ip,
                                    ctypes.POINTER(ctypes.c_size_t)]

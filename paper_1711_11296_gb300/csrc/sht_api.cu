@@ -59,7 +59,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 void free_plan_memory(sht_plan_s* p) {
     void* ptrs[] = {p->d_mu, p->d_sin, p->d_w, p->d_w_over_I, p->d_eps, p->d_amm,
                     p->d_pnm, p->d_rev, p->d_tw, p->d_twpost, p->d_twpass, p->d_work,
-                    p->d_tiles_fwd, p->d_tiles_inv, p->d_status, p->d_jmin};
+                    p->d_tiles_fwd, p->d_tiles_inv, p->d_status, p->d_jmin,
+                    p->d_spec_pad};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->split) split_tables_destroy(p);

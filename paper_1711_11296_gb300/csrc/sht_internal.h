@@ -124,6 +124,7 @@ struct sht_plan_s {
 
     int* d_status;             // device status word: kernels OR in failure bits
                                // (1: tensor-core wait timed out, 2: FFT wait timed out)
+    void* d_spec_pad;          // spectrum-sized buffer of sht_prolong_spectral (on first use)
     int* d_jmin;               // FP64 plans with the reduced transform: [2(N+1)]
                                // first node with some |P~| >= 1e-16 (null: off)
     sht::SplitTables* split;   // null for FP64 plans

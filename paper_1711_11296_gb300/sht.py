@@ -114,6 +114,30 @@ class Plan:
                                       _stream_ptr(self.device)))
         return out
 
+    def prolong_spectral(self, coarse_spec, Nc, out=None):
+        """Grid of a spectrum truncated at Nc <= N, zero-padded to this plan's
+        N (multigrid prolongation in spectral space, Appendix C)."""
+        self._check(coarse_spec, ((Nc + 1) * (Nc + 2) // 2, self.F), self.complex_dtype,
+                    "coarse_spec")
+        out = self.empty_grid() if out is None else out
+        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        check(lib.sht_prolong_spectral(self._h, ctypes.c_void_p(coarse_spec.data_ptr()), Nc,
+                                       ctypes.c_void_p(out.data_ptr()),
+                                       _stream_ptr(self.device)))
+        return out
+
+    def inject_nested(self, fine_grid, k, out=None):
+        """This plan's grid sampled from a nested fine grid (every 2^k-th
+        latitude and longitude: restriction by injection, Appendix C)."""
+        Jf, If = 2 ** k * (self.J + 1) - 1, 2 ** k * self.I
+        self._check(fine_grid, (self.F, Jf, If), self.real_dtype, "fine_grid")
+        out = self.empty_grid() if out is None else out
+        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        check(lib.sht_inject_nested(self._h, ctypes.c_void_p(fine_grid.data_ptr()), k,
+                                    ctypes.c_void_p(out.data_ptr()),
+                                    _stream_ptr(self.device)))
+        return out
+
     def tables(self):
         """(w [J], mu [J], pnm [ncoef, (J+1)/2]) copied from the device."""
         import numpy as np
