@@ -372,12 +372,12 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
     }
 }
 
-// The same with the shape a compile-time constant (pass P onwards).
-template <typename T, int L, int P>
+// The same with the shape a compile-time constant (passes P .. END-1).
+template <typename T, int L, int P, int END = FacOf<L, sizeof(T) == 8>::v.npass>
 __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int nrows, int LP,
                                              const typename Vec2<T>::type* twp) {
     constexpr FftShape F = FacOf<L, sizeof(T) == 8>::v;
-    if constexpr (P < F.npass) {
+    if constexpr (P < END) {
         constexpr int R = F.radix[P];
         constexpr int M = F.span[P];
         constexpr int S = R * M;
@@ -392,7 +392,35 @@ __device__ __forceinline__ void passes_fixed(typename Vec2<T>::type* rows, int n
             bfly_fixed<T, R, M>(rows + (size_t)row * LP, blk * S + n1, twp + OFF, n1);
         }
         __syncthreads();
-        passes_fixed<T, L, P + 1>(rows, nrows, LP, twp);
+        passes_fixed<T, L, P + 1, END>(rows, nrows, LP, twp);
+    }
+}
+
+// FP32 two-pass shapes L = Q x 32 with Q >= 8: the forward runs its first
+// pass from the grid rows (below), the inverse its last pass into them.
+template <typename T, int L>
+__host__ __device__ constexpr bool first_pass_from_global() {
+    if constexpr (sizeof(T) != 4 || L <= 0) {
+        return false;
+    } else {
+        constexpr FftShape F = FacOf<L, false>::v;
+        return F.npass == 2 && F.radix[1] == 32 && F.span[0] == 32 && F.radix[0] >= 8;
+    }
+}
+
+// FP32 two-pass shapes L = Q x 32 with Q >= 8: the inverse runs its last
+// pass (radix 32, span 1) straight into the grid rows.  Butterfly b of a
+// row holds frequencies b + Q k1 (k1 < 32) of the digit-reversed output,
+// so for each k1 the lanes of a warp store consecutive complex values
+// (at least 64 contiguous bytes), and the result needs no shared-memory
+// round trip before the store.
+template <typename T, int L>
+__host__ __device__ constexpr bool inverse_stores_from_last_pass() {
+    if constexpr (sizeof(T) != 4 || L <= 0) {
+        return false;
+    } else {
+        constexpr FftShape F = FacOf<L, false>::v;
+        return F.npass == 2 && F.radix[1] == 32 && F.radix[0] >= 8;
     }
 }
 
@@ -513,28 +541,73 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
                (long long)j * A.src.row_stride;
     };
 
-    {
-        // element k of row r goes to rows[r LP + ph(k)], copied
-        // asynchronously so that all of the CTA's loads are in flight
-        const int s = A.src.elem_stride;
-        for (int r = 0; r < nrows; ++r) {
-            const T* x = row_ptr(r);
-            V* d = rows + (size_t)r * LP;
-            for (int k = tid; k < L; k += NT) {
-                if (!STRIDED) {
-                    cp_async<sizeof(V)>(d + ph<T>(k), reinterpret_cast<const V*>(x) + k);
-                } else {
-                    cp_async<sizeof(T)>(&d[ph<T>(k)].x, x + (long long)(2 * k) * s);
-                    cp_async<sizeof(T)>(&d[ph<T>(k)].y, x + (long long)(2 * k + 1) * s);
+    if constexpr (!STRIDED && first_pass_from_global<T, LT>()) {
+        // The first pass (radix Q, span 32) reads its inputs straight from
+        // the grid rows into registers: butterfly n1 of a row takes
+        // z[n1 + 32 t], t < Q, so for each t the lanes of a warp load 256
+        // contiguous bytes.  Only the twiddle table is copied
+        // asynchronously; the first butterfly's loads are in flight while
+        // the CTA waits for it.
+        constexpr FftShape FS = FacOf<LT, false>::v;
+        constexpr int Q = FS.radix[0];
+        constexpr int M = FS.span[0];                                  // 32
+        constexpr int STEP = M + (M >> PadShift<T>::value);            // padded
+        load_twiddles_async(tws, A.twp, FS.twtotal);
+        const int total = nrows * M;
+        V a[Q];
+        auto load = [&](int idx) {
+            const int r = idx / M, n1 = idx - r * M;
+            const V* x = reinterpret_cast<const V*>(row_ptr(r)) + n1;
+#pragma unroll
+            for (int t = 0; t < Q; ++t) a[t] = x[t * M];
+        };
+        auto finish = [&](int idx) {
+            const int r = idx / M, n1 = idx - r * M;
+            Dft<T, Q>::run(a);
+            if (n1 != 0) {
+#pragma unroll
+                for (int k1 = 1; k1 < Q; ++k1)
+                    a[Dft<T, Q>::pos(k1)] =
+                        K::mul(a[Dft<T, Q>::pos(k1)], tws[(k1 - 1) * M + n1]);
+            }
+            V* zb = rows + (size_t)r * LP + n1;
+#pragma unroll
+            for (int k1 = 0; k1 < Q; ++k1) zb[k1 * STEP] = a[Dft<T, Q>::pos(k1)];
+        };
+        if (tid < total) load(tid);
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid < total) finish(tid);
+        for (int idx = tid + NT; idx < total; idx += NT) {
+            load(idx);
+            finish(idx);
+        }
+        __syncthreads();
+        passes_fixed<T, LT, 1>(rows, nrows, LP, tws);
+    } else {
+        {
+            // element k of row r goes to rows[r LP + ph(k)], copied
+            // asynchronously so that all of the CTA's loads are in flight
+            const int s = A.src.elem_stride;
+            for (int r = 0; r < nrows; ++r) {
+                const T* x = row_ptr(r);
+                V* d = rows + (size_t)r * LP;
+                for (int k = tid; k < L; k += NT) {
+                    if (!STRIDED) {
+                        cp_async<sizeof(V)>(d + ph<T>(k), reinterpret_cast<const V*>(x) + k);
+                    } else {
+                        cp_async<sizeof(T)>(&d[ph<T>(k)].x, x + (long long)(2 * k) * s);
+                        cp_async<sizeof(T)>(&d[ph<T>(k)].y, x + (long long)(2 * k + 1) * s);
+                    }
                 }
             }
+            load_twiddles_async(tws, A.twp,
+                                LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
+            cp_async_wait_all();
         }
-        load_twiddles_async(tws, A.twp,
-                            LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
-        cp_async_wait_all();
+        __syncthreads();
+        run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
     }
-    __syncthreads();
-    run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
     const int nout = (A.N + 1) * nf;
     const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
@@ -703,9 +776,30 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         }
     }
     __syncthreads();
+    const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
+    if constexpr (inverse_stores_from_last_pass<T, LT>()) {
+        constexpr FftShape FS = FacOf<LT, false>::v;
+        constexpr int R = FS.radix[1];   // 32 = the padding period: one padded
+        constexpr int Q = FS.radix[0];   // index per butterfly
+        passes_fixed<T, LT, 0, 1>(rows, nrows, LP, tws);
+        const V sgn = K::make(rs, -rs);   // x = conj(z) rs
+        for (int idx = tid; idx < nrows * Q; idx += NT) {
+            const int r = idx / Q, b = idx - r * Q;
+            const int f = f0 + (r < nf ? r : r - nf);
+            const int j = (r < nf) ? jh : (A.J - 1 - jh);
+            V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I) + b;
+            const V* zb = rows + (size_t)r * LP + ph<T>(b * R);
+            V a[R];
+#pragma unroll
+            for (int t = 0; t < R; ++t) a[t] = zb[t];
+            Dft<T, R>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) xv[k1 * Q] = mul_f32x2(a[Dft<T, R>::pos(k1)], sgn);
+        }
+        return;
+    }
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
-    const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
     for (int r = 0; r < nrows; ++r) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
