@@ -718,6 +718,24 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     const bool equator = (jh == A.Jh - 1);
     const int nrows = equator ? nf : 2 * nf;
     const int tid = threadIdx.x;
+    const int half = L / 2;
+    // Loads whose values are needed only after the copies below (the row
+    // scale and, for compile-time lengths, the real-spectrum twiddles of the
+    // thread's packing frequencies q and L - q), issued first so that their
+    // latency hides behind the copies.
+    const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
+    constexpr int NQ = LT > 0 ? (LT / 2 + NT) / NT : 1;
+    V twq[NQ], twc[NQ];
+    if constexpr (LT > 0) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = tid + i * NT;
+            if (q <= half) {
+                twq[i] = A.twpost[q];
+                twc[i] = A.twpost[q == 0 ? 0 : L - q];
+            }
+        }
+    }
 
     load_twiddles(tws, A.twp, LT > 0 ? FacOf<LT, sizeof(T) == 8>::v.twtotal : A.shape.twtotal);
     // unfold S/A into the two hemispheres' zonal spectra Y_m, m <= N
@@ -739,21 +757,21 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     // N are never read), then the Hermitian packing
     //   Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q}),
     // stored as conj(Z) in place.
-    const int half = L / 2;
     const int N = A.N;
     const T mf1 = (T)A.mfactor1;
     auto pack = [&](V y, V yc, V wv) -> V {
         return K::conj(K::add(K::add(y, K::conj(yc)),
                               K::mul_pi(K::mul(wv, K::sub(y, K::conj(yc))))));
     };
-    for (int q = tid; q <= half; q += NT) {
+    // frequencies q and L - q with the twiddles W_I^q and W_I^{L-q}
+    auto pack_q = [&](int q, V tq, V tc) {
         const int qc = L - q;   // >= q, as q <= L/2
         const int pq = ph<T>(q), pc = ph<T>(qc);
         const bool hq = q <= N, hc = q != 0 && qc <= N;
         const bool pair = q != 0 && q != qc;
         const T fq = q == 0 ? (T)1 : mf1, fc = mf1;
-        const V wq = K::conj(A.twpost[q]);
-        const V wc = pair ? K::conj(A.twpost[qc]) : wq;
+        const V wq = K::conj(tq);
+        const V wc = pair ? K::conj(tc) : wq;
         const V zero = K::make((T)0, (T)0);
         for (int fl = 0; fl < nf; ++fl) {
             V* zn = rows + (size_t)fl * LP;
@@ -774,9 +792,18 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
                 if (!equator) zs[pc] = pack(ysc, ysq, wc);
             }
         }
+    };
+    if constexpr (LT > 0) {
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) {
+            const int q = tid + i * NT;
+            if (q <= half) pack_q(q, twq[i], twc[i]);
+        }
+    } else {
+        for (int q = tid; q <= half; q += NT)
+            pack_q(q, A.twpost[q], A.twpost[q == 0 ? 0 : L - q]);
     }
     __syncthreads();
-    const T rs = A.rowscale ? (T)A.rowscale[jh] : (T)1;
     if constexpr (inverse_stores_from_last_pass<T, LT>()) {
         constexpr FftShape FS = FacOf<LT, false>::v;
         constexpr int R = FS.radix[1];   // 32 = the padding period: one padded
