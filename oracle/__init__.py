@@ -22,6 +22,10 @@ Contents (all FP64 except the binary128 Legendre recurrence of Sec. 4.1):
 * ``analysis``, ``synthesis``      -- Eq. (dSHT)/(cc-quad), Eq. (iSHT)/(iLT)
 * ``adjoint_analysis``, ``adjoint_synthesis`` -- transposes of the two
 * ``restrict_nested``              -- Sec. 3.2 / Appendix C
+* ``reduced_sizes``, ``analysis_reduced``, ``synthesis_reduced`` -- reduced
+                                      Clenshaw-Curtis grids with per-latitude
+                                      longitude counts (the reduction rule
+                                      quoted in Sec. 6)
 """
 from .cc_oracle import *  # noqa: F401,F403
 from .cc_oracle import __all__  # noqa: F401

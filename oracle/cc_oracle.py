@@ -34,7 +34,9 @@ __all__ = [
     "synthesis", "adjoint_analysis", "adjoint_synthesis", "restrict_nested",
     "analysis_gauss", "synthesis_gauss", "legendre_forward_m",
     "legendre_inverse_m", "nested_rows", "fejer1_nodes", "fejer1_weights",
-    "analysis_fejer1", "synthesis_fejer1",
+    "analysis_fejer1", "synthesis_fejer1", "reduced_sizes",
+    "reduced_row_offsets", "reduced_kmax", "analysis_reduced",
+    "synthesis_reduced",
 ]
 
 _lib = None
@@ -420,3 +422,97 @@ def orthonormality_errors(N, J, m, pnm=None, w=None):
 
 
 __all__ += ["orthonormality_errors", "cc_node_binary128", "synthesis_rows"]
+
+
+# --------------------------------------------------------------------------
+# Reduced Clenshaw-Curtis grids (per-latitude longitude counts, Sec. 6)
+# --------------------------------------------------------------------------
+def _even_smooth_ceil(x):
+    """Smallest even n >= x whose half has no prime factor other than 2, 3,
+    5 (so that its half-length FFT factors into radices 2, 3, 4, 5, 8)."""
+    n = max(2, int(np.ceil(x)))
+    while True:
+        if n % 2 == 0:
+            h = n // 2
+            for p in (2, 3, 5):
+                while h % p == 0:
+                    h //= p
+            if h == 1:
+                return n
+        n += 1
+
+
+def reduced_sizes(N, J, I, thr=1e-16):
+    """Longitude counts I_j of the reduced Clenshaw-Curtis grid.
+
+    Sec. 6 quotes the reduction rule of the JMA model: latitude j carries at
+    least 4 M_j + 1 longitudes, M_j being the zonal wavenumber beyond which
+    every |P~_n^m(mu_j)| (0 <= n <= N) is below 1e-16.  Read here as:
+    M_j = the largest m with some |P~_n^m(mu_j)| >= 1e-16, and I_j = the
+    smallest even 2-3-5-smooth count >= 4 M_j + 1, capped at the full grid's
+    I.  Returns (I_j [J], M_j [J]) with j = 1 first; the P~ come from the
+    binary128 recurrence rounded to FP64."""
+    P = pnm_cc(N, J)                                   # [ncoef][J]
+    M = np.zeros(J, dtype=np.int64)
+    for m in range(N + 1):
+        r0 = coef_offset(N, m)
+        sig = np.any(np.abs(P[r0:r0 + N - m + 1]) >= thr, axis=0)
+        M[sig] = m
+    Ij = np.array([min(I, _even_smooth_ceil(4 * int(Mj) + 1)) for Mj in M], dtype=np.int64)
+    return Ij, M
+
+
+def reduced_row_offsets(Ij):
+    """First point of each latitude row in a field's packed rows."""
+    Ij = np.asarray(Ij, dtype=np.int64)
+    return np.concatenate([[0], np.cumsum(Ij)])
+
+
+def reduced_kmax(N, Ij):
+    """Largest zonal wavenumber carried on each latitude: min(N, I_j/2 - 1)
+    (the Nyquist wavenumber I_j/2 is not a Fourier mode of a real row)."""
+    return np.minimum(N, np.asarray(Ij, dtype=np.int64) // 2 - 1)
+
+
+def analysis_reduced(x, N, J, Ij):
+    """Forward SHT on a reduced Clenshaw-Curtis grid.
+
+    x: real [F][sum I_j], latitude rows packed one after another (j = 1
+    first).  Row j gives X^m(phi_j) by the zonal DFT of its I_j points
+    (discretised Eq. dFT with 1/I_j) for m <= min(N, I_j/2 - 1), and 0 above;
+    then the quadrature of Eq. (cc-quad) over all J nodes.  Returns the
+    packed spectrum [ncoef][F]."""
+    x = np.asarray(x, dtype=np.float64)
+    F = x.shape[0]
+    off = reduced_row_offsets(Ij)
+    K = reduced_kmax(N, Ij)
+    X = np.zeros((F, J, N + 1), dtype=np.complex128)
+    for j in range(J):
+        row = x[:, off[j]:off[j + 1]]
+        X[:, j, :K[j] + 1] = dft_forward(row, int(K[j]))
+    w = cc_weights(J)
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m in range(N + 1):
+        a = legendre_forward_m(X[:, :, m], pnm_cc(N, J, m, m), w)
+        if m == 0:
+            a = a.real + 0j
+        spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
+    return spec
+
+
+def synthesis_reduced(spec, N, J, Ij):
+    """Inverse SHT (Eq. iSHT via Eq. iLT) on a reduced Clenshaw-Curtis grid:
+    X^m(phi_j) for every node, then row j is the inverse zonal DFT of
+    m <= min(N, I_j/2 - 1) on its I_j longitudes.  Returns [F][sum I_j]."""
+    spec = np.asarray(spec, dtype=np.complex128)
+    F = spec.shape[1]
+    X = np.zeros((F, J, N + 1), dtype=np.complex128)
+    for m in range(N + 1):
+        a = spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
+        X[:, :, m] = legendre_inverse_m(a, pnm_cc(N, J, m, m))
+    off = reduced_row_offsets(Ij)
+    K = reduced_kmax(N, Ij)
+    out = np.zeros((F, int(off[-1])), dtype=np.float64)
+    for j in range(J):
+        out[:, off[j]:off[j + 1]] = dft_inverse(X[:, j, :K[j] + 1], int(Ij[j]))
+    return out
