@@ -265,6 +265,42 @@ int sht_plan_autotune(sht_plan_t plan, int reps, void* stream, int* fields_per_c
  * setting, since the set of tiles does not change. */
 int sht_plan_set_reduced(sht_plan_t plan, int on);
 
+/* Reduced Clenshaw-Curtis grids (Sec. 6 proposes reduced and octahedral
+ * grids on the Clenshaw-Curtis latitudes).  Latitude j (0-based from the
+ * north) carries its own number I_lat[j] of equispaced longitudes
+ * lambda_i = 2 pi i / I_lat[j].
+ *
+ * sht_reduced_grid_sizes applies the reduction rule Sec. 6 quotes (at
+ * least 4 M_j + 1 longitudes, M_j the zonal wavenumber beyond which every
+ * |P~_n^m(mu_j)| is below 1e-16) to any plan's P~ table: M_j = the largest
+ * m with some |P~_n^m(mu_j)| >= 1e-16, and I_lat[j] = the smallest even
+ * count >= 4 M_j + 1 whose half has no prime factor above 5, capped at the
+ * plan's I.  I_lat: host array of J ints, written.  Synchronous.
+ *
+ * sht_plan_create_reduced creates a plan on the Clenshaw-Curtis latitudes
+ * of J nodes with I_lat[j] longitudes on latitude j (host array of J ints,
+ * copied; each even, <= 8192, with I_lat[j]/2 a product of 2, 3 and 5, and
+ * symmetric about the Equator; the largest must exceed 2N).  Grids of the
+ * plan are device arrays [nfields][P] of P = sum_j I_lat[j] points, row j
+ * (all its longitudes) after row j-1.  Row j carries the zonal wavenumbers
+ * m <= min(N, I_lat[j]/2 - 1): the forward transform takes X^m(phi_j) from
+ * the zonal DFT of the row's points (Eq. dFT with 1/I_lat[j]) and zero
+ * above that range, then the quadrature of Eq. (cc-quad); the inverse
+ * synthesises that range of Eq. (iSHT) on each row.  sht_forward,
+ * sht_inverse, sht_adjoint (the transposes for the plain inner products),
+ * sht_prolong_spectral, sht_plan_set_reduced, the tuning calls and
+ * sht_plan_status take such plans; sht_restrict_nested and
+ * sht_inject_nested return SHT_ERR_NOT_NESTED and grouped launches
+ * SHT_ERR_UNSUPPORTED.  Errors as sht_plan_create_grid; SHT_ERR_ARG for a
+ * bad I_lat.
+ *
+ * sht_plan_grid_points writes the points per field of any plan's grid
+ * (sum_j I_lat[j] for a reduced plan, J I otherwise). */
+int sht_reduced_grid_sizes(sht_plan_t plan, int* I_lat);
+int sht_plan_create_reduced(int N, int J, const int* I_lat, int nfields, int precision,
+                            sht_plan_t* out);
+int sht_plan_grid_points(sht_plan_t plan, long long* npts);
+
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles
  * (cos theta_j); pnm: ncoef x (J+1)/2 doubles, rows in spectrum order,

@@ -19,7 +19,8 @@ EXPORTED = [
     "sht_group_destroy", "sht_group_forward", "sht_group_inverse",
     "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
     "sht_plan_create_grid", "sht_plan_set_reduced", "sht_prolong_spectral",
-    "sht_inject_nested",
+    "sht_inject_nested", "sht_reduced_grid_sizes", "sht_plan_create_reduced",
+    "sht_plan_grid_points",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -75,6 +76,9 @@ def _load():
     lib.sht_plan_set_tuning.argtypes = [vp, i, i]
     lib.sht_plan_get_tuning.argtypes = [vp, ip, ip]
     lib.sht_plan_autotune.argtypes = [vp, i, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
+    lib.sht_reduced_grid_sizes.argtypes = [vp, ip]
+    lib.sht_plan_create_reduced.argtypes = [i, i, ip, i, i, ctypes.POINTER(vp)]
+    lib.sht_plan_grid_points.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.sht_last_error.restype = ctypes.c_char_p
     lib.sht_version.restype = ctypes.c_char_p
     for name in EXPORTED:

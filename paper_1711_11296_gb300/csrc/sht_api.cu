@@ -64,6 +64,10 @@ void free_plan_memory(sht_plan_s* p) {
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->split) split_tables_destroy(p);
+    if (p->ragged) {
+        ragged_free(p->ragged);
+        p->ragged = nullptr;
+    }
     if (p->prof) {
         for (auto& r : p->prof->recs) {
             cudaEventDestroy(r.a);
@@ -431,6 +435,10 @@ extern "C" int sht_restrict_nested(sht_plan_t p, const void* fine_grid, int k,
     int rc = check_plan(p);
     if (rc) return rc;
     if (!fine_grid || !coarse_spec) { set_error("NULL buffer"); return SHT_ERR_ARG; }
+    if (p->ragged) {
+        set_error("a reduced grid (per-latitude longitudes) does not nest");
+        return SHT_ERR_NOT_NESTED;
+    }
     if (p->grid != SHT_GRID_CC) {
         set_error("the shifted (Fejer first-rule) grid does not nest (Sec. 3.3)");
         return SHT_ERR_NOT_NESTED;

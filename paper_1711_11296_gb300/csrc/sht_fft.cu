@@ -449,6 +449,7 @@ struct FwdArgs {
     const double* rowscale;
     double mscale0, mscale1;
     unsigned* colmax;   // FP16 split plans: max |output| per real column (float bits)
+    const long long* rowoff;   // reduced grid: first point of each row (null: regular)
     int F, J, Jh, L, LP, N, G;
     FftShape shape;
 };
@@ -463,6 +464,8 @@ struct InvArgs {
     const int* rev;
     const double* rowscale;
     double mfactor1;
+    const long long* rowoff;   // reduced grid: first point of each row (null: regular)
+    long long fstride;         // reduced grid: points per field
     int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
@@ -537,6 +540,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     auto row_ptr = [&](int r) -> const T* {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
+        if (LT == 0 && A.rowoff) return A.grid + (long long)f * A.src.field_stride + A.rowoff[j];
         return A.grid + (long long)f * A.src.field_stride + A.src.row_offset +
                (long long)j * A.src.row_stride;
     };
@@ -646,15 +650,26 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     const T sc0 = (T)0.5 * rs * (T)A.mscale0, sc1 = (T)0.5 * rs * (T)A.mscale1;
     // two outputs (m, fl) per iteration, idx and idx + NT, with all shared-
     // memory reads of both issued before any arithmetic
+    // A reduced-grid row of half-length L carries the wavenumbers up to
+    // min(N, L - 1); those above are written as zeros (computed at the
+    // clamped wavenumber, then discarded).
+    const int kmax = (LT == 0 && A.rowoff) ? min(A.N, L - 1) : A.N;
+    auto clampk = [&](int m) -> int {
+        if constexpr (LT > 0)
+            return m;
+        else
+            return min(m, kmax);
+    };
     Walk2 wa(tid, nf), wb(tid + NT, nf);
     for (; wa.major * nf + wa.minor < nout; wa.next(), wa.next(), wb.next(), wb.next()) {
         const bool hb = wb.major * nf + wb.minor < nout;
         const int ma = wa.major, fa = wa.minor;
         const int mb = hb ? wb.major : ma, fb = hb ? wb.minor : fa;
-        const int pma = ph<T>(rev_of<T, LT>(ma, A.rev));
-        const int pca = ph<T>(rev_of<T, LT>(ma == 0 ? 0 : L - ma, A.rev));
-        const int pmb = ph<T>(rev_of<T, LT>(mb, A.rev));
-        const int pcb = ph<T>(rev_of<T, LT>(mb == 0 ? 0 : L - mb, A.rev));
+        const int ra = clampk(ma), rb = clampk(mb);
+        const int pma = ph<T>(rev_of<T, LT>(ra, A.rev));
+        const int pca = ph<T>(rev_of<T, LT>(ra == 0 ? 0 : L - ra, A.rev));
+        const int pmb = ph<T>(rev_of<T, LT>(rb, A.rev));
+        const int pcb = ph<T>(rev_of<T, LT>(rb == 0 ? 0 : L - rb, A.rev));
         const V* na = rows + (size_t)fa * LP;
         const V* nb = rows + (size_t)fb * LP;
         const V a_nm = na[pma], a_nc = na[pca], b_nm = nb[pmb], b_nc = nb[pcb];
@@ -667,7 +682,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             b_sm = sb[pmb];
             b_sc = sb[pcb];
         }
-        const V wta = A.twpost[ma], wtb = A.twpost[mb];
+        const V wta = A.twpost[ra], wtb = A.twpost[rb];
         const T sca = ma == 0 ? sc0 : sc1;
         const T scb = mb == 0 ? sc0 : sc1;
         const V xan = real_spec(a_nm, a_nc, wta), xbn = real_spec(b_nm, b_nc, wtb);
@@ -679,13 +694,15 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             Sb = K::add(xbn, xbs);
             Ab = K::sub(xbn, xbs);
         }
-        const V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
+        V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
+        if (ra != ma) osa = oaa = K::make((T)0, (T)0);
         const size_t basea = ((size_t)ma * 2 * A.Jh + jh) * A.F + f0 + fa;
         A.work[basea] = osa;
         A.work[basea + (size_t)A.Jh * A.F] = oaa;
         if (track) record(fa, osa, oaa);
         if (hb) {
-            const V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
+            V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
+            if (rb != mb) osb = oab = K::make((T)0, (T)0);
             const size_t baseb = ((size_t)mb * 2 * A.Jh + jh) * A.F + f0 + fb;
             A.work[baseb] = osb;
             A.work[baseb + (size_t)A.Jh * A.F] = oab;
@@ -741,7 +758,10 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     // unfold S/A into the two hemispheres' zonal spectra Y_m, m <= N
     // (S lands in the northern row, A in the southern one, copied
     // asynchronously; then both hemispheres are formed in place)
-    const int nin = (A.N + 1) * nf;
+    // a reduced-grid row of half-length L carries the wavenumbers up to
+    // min(N, L - 1) (Y_m = 0 above)
+    const int kmax = (LT == 0 && A.rowoff) ? min(A.N, L - 1) : A.N;
+    const int nin = (kmax + 1) * nf;
     for (Walk2 w(tid, nf); w.major * nf + w.minor < nin; w.next()) {
         const int m = w.major, fl = w.minor;
         const size_t base = ((size_t)m * 2 * A.Jh + jh) * A.F + f0 + fl;
@@ -753,11 +773,10 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     cp_async_wait_all();
     __syncthreads();
     // One thread owns frequencies (q, L-q) of all fields in both hemispheres
-    // Y_m = fac (S_m +- A_m) (Y_0 real, Y_m = 0 for m > N; stale slots beyond
-    // N are never read), then the Hermitian packing
+    // Y_m = fac (S_m +- A_m) (Y_0 real, Y_m = 0 for m > kmax; stale slots
+    // beyond kmax are never read), then the Hermitian packing
     //   Z_q = (Y_q + conj Y_{L-q}) + i conj(W_I^q) (Y_q - conj Y_{L-q}),
     // stored as conj(Z) in place.
-    const int N = A.N;
     const T mf1 = (T)A.mfactor1;
     auto pack = [&](V y, V yc, V wv) -> V {
         return K::conj(K::add(K::add(y, K::conj(yc)),
@@ -767,7 +786,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     auto pack_q = [&](int q, V tq, V tc) {
         const int qc = L - q;   // >= q, as q <= L/2
         const int pq = ph<T>(q), pc = ph<T>(qc);
-        const bool hq = q <= N, hc = q != 0 && qc <= N;
+        const bool hq = q <= kmax, hc = q != 0 && qc <= kmax;
         const bool pair = q != 0 && q != qc;
         const T fq = q == 0 ? (T)1 : mf1, fc = mf1;
         const V wq = K::conj(tq);
@@ -777,7 +796,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
             V* zn = rows + (size_t)fl * LP;
             V* zs = rows + (size_t)(nf + fl) * LP;
             // S and A at frequencies q and L - q, each read once (zero above
-            // N; Y_L = 0 for q = 0)
+            // kmax; Y_L = 0 for q = 0)
             const V Sq = hq ? zn[pq] : zero;
             const V Aq = (hq && !equator) ? zs[pq] : zero;
             const V Sc = hc ? zn[pc] : zero;
@@ -830,7 +849,9 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     for (int r = 0; r < nrows; ++r) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
-        V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I);
+        V* xv = reinterpret_cast<V*>(
+            (LT == 0 && A.rowoff) ? A.grid + (long long)f * A.fstride + A.rowoff[j]
+                                  : A.grid + ((long long)f * A.J + j) * A.I);
         const V* z = rows + (size_t)r * LP;
         if constexpr (LT > 0) {
             // all of the thread's shared-memory reads of the row first
@@ -896,6 +917,50 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     inv_body<T, 0>(G.a[p], local % G.nfg[p], local / G.nfg[p]);
 }
 
+// ---- reduced grids: a half-length per latitude pair -------------------
+// Each CTA takes its latitude pair's FFT shape and the offsets of that
+// shape's tables; rows, shared memory and the row pitch are sized for the
+// longest row of the grid.
+template <typename T> struct RaggedFwd {
+    FwdArgs<T> a;
+    const RShape* shapes;
+    const int* shape_of;
+};
+
+template <typename T> struct RaggedInv {
+    InvArgs<T> a;
+    const RShape* shapes;
+    const int* shape_of;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_forward_ragged_kernel(const __grid_constant__ RaggedFwd<T> R) {
+    const int jh = blockIdx.y;
+    const RShape& rs = R.shapes[R.shape_of[jh]];
+    FwdArgs<T> A = R.a;
+    A.shape = rs.sh;
+    A.L = rs.sh.L;
+    A.twp += rs.tw_off;
+    A.twpost += rs.post_off;
+    A.rev += rs.rev_off;
+    fwd_body<T, 0, false>(A, blockIdx.x, jh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    fft_inverse_ragged_kernel(const __grid_constant__ RaggedInv<T> R) {
+    const int jh = blockIdx.y;
+    const RShape& rs = R.shapes[R.shape_of[jh]];
+    InvArgs<T> A = R.a;
+    A.shape = rs.sh;
+    A.L = rs.sh.L;
+    A.twp += rs.tw_off;
+    A.twpost += rs.post_off;
+    A.rev += rs.rev_off;
+    inv_body<T, 0>(A, blockIdx.x, jh);
+}
+
 template <typename T, int LT>
 cudaError_t fwd_launch(const FwdArgs<T>& A, bool strided, dim3 grid, size_t smem,
                        cudaStream_t s) {
@@ -947,6 +1012,7 @@ FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource&
     A.mscale0 = sc.mscale0;
     A.mscale1 = sc.mscale1;
     A.colmax = p->d_colmax;
+    A.rowoff = nullptr;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
@@ -980,6 +1046,8 @@ InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& 
     A.rev = p->d_rev;
     A.rowscale = sc.rowscale;
     A.mfactor1 = sc.mfactor1;
+    A.rowoff = nullptr;
+    A.fstride = (long long)p->J * p->I;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
@@ -995,6 +1063,56 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
 #define SHT_INV(LV) inv_launch<T, LV>(A, g, p->fft_smem, s)
     SHT_FFT_DISPATCH(p->fft.L, SHT_INV)
 #undef SHT_INV
+}
+
+template <typename T>
+cudaError_t fwd_ragged_impl(const sht_plan_s* p, const void* grid, const FwdScale& sc,
+                            void* work, cudaStream_t s) {
+    using V = typename Vec2<T>::type;
+    const RaggedGrid* rg = p->ragged;
+    RowSource src;
+    src.field_stride = rg->npts;
+    src.row_stride = 0;
+    src.row_offset = 0;
+    src.elem_stride = 1;
+    RaggedFwd<T> R;
+    R.a = make_fwd_args<T>(p, grid, src, sc, work);
+    R.a.rowoff = rg->d_rowoff;
+    R.a.twp = static_cast<const V*>(rg->d_twpass);
+    R.a.twpost = static_cast<const V*>(rg->d_twpost);
+    R.a.rev = rg->d_rev;
+    R.shapes = rg->d_shapes;
+    R.shape_of = rg->d_shape_of;
+    if (R.a.colmax) {
+        const cudaError_t e = cudaMemsetAsync(R.a.colmax, 0, 2 * (size_t)p->F * sizeof(unsigned), s);
+        if (e) return e;
+    }
+    cudaError_t e = ensure_smem((const void*)fft_forward_ragged_kernel<T>, p->fft_smem);
+    if (e) return e;
+    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
+    fft_forward_ragged_kernel<T><<<g, NT, p->fft_smem, s>>>(R);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t inv_ragged_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
+                            void* grid, cudaStream_t s) {
+    using V = typename Vec2<T>::type;
+    const RaggedGrid* rg = p->ragged;
+    RaggedInv<T> R;
+    R.a = make_inv_args<T>(p, work, sc, grid);
+    R.a.rowoff = rg->d_rowoff;
+    R.a.fstride = rg->npts;
+    R.a.twp = static_cast<const V*>(rg->d_twpass);
+    R.a.twpost = static_cast<const V*>(rg->d_twpost);
+    R.a.rev = rg->d_rev;
+    R.shapes = rg->d_shapes;
+    R.shape_of = rg->d_shape_of;
+    cudaError_t e = ensure_smem((const void*)fft_inverse_ragged_kernel<T>, p->fft_smem);
+    if (e) return e;
+    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
+    fft_inverse_ragged_kernel<T><<<g, NT, p->fft_smem, s>>>(R);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -1100,12 +1218,20 @@ size_t fft_smem_bytes(int I, int G, bool fp64) {
 cudaError_t launch_fft_forward(const sht_plan_s* p, const void* grid,
                                const RowSource& src, const FwdScale& sc,
                                void* work, cudaStream_t s) {
+    if (p->ragged) {
+        if (p->prec == SHT_FP64) return fwd_ragged_impl<double>(p, grid, sc, work, s);
+        return fwd_ragged_impl<float>(p, grid, sc, work, s);
+    }
     if (p->prec == SHT_FP64) return fwd_impl<double>(p, grid, src, sc, work, s);
     return fwd_impl<float>(p, grid, src, sc, work, s);
 }
 
 cudaError_t launch_fft_inverse(const sht_plan_s* p, const void* work,
                                const InvScale& sc, void* grid, cudaStream_t s) {
+    if (p->ragged) {
+        if (p->prec == SHT_FP64) return inv_ragged_impl<double>(p, work, sc, grid, s);
+        return inv_ragged_impl<float>(p, work, sc, grid, s);
+    }
     if (p->prec == SHT_FP64) return inv_impl<double>(p, work, sc, grid, s);
     return inv_impl<float>(p, work, sc, grid, s);
 }

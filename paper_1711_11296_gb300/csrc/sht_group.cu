@@ -112,6 +112,10 @@ extern "C" int sht_group_create(const sht_plan_t* plans, int nplans, sht_group_t
             set_error("plan %d is invalid or destroyed", q);
             return SHT_ERR_HANDLE;
         }
+        if (plans[q]->ragged) {
+            set_error("plan %d has a reduced grid; grouped launches take regular grids", q);
+            return SHT_ERR_UNSUPPORTED;
+        }
         if (plans[q]->prec != plans[0]->prec || plans[q]->device != plans[0]->device) {
             set_error("plans of a group must share precision and device");
             return SHT_ERR_ARG;

@@ -74,6 +74,28 @@ struct InvScale {
 
 struct SplitTables;   // tensor-core operand tables (split plans)
 
+// Reduced grid: latitude j carries its own number I_j of longitudes.  The
+// distinct half-lengths L = I_j/2 each have an FFT shape and tables; their
+// tables are concatenated in device buffers at the offsets below.
+struct RShape {
+    FftShape sh;
+    long long tw_off;     // per-pass twiddle tables (entries)
+    long long post_off;   // e^{-2 pi i q / I_j}, q < L (entries)
+    long long rev_off;    // digit-reversed positions (entries)
+};
+
+struct RaggedGrid {
+    std::vector<int> Ij;             // [J] longitudes per latitude, j = 0 northernmost
+    long long npts = 0;              // grid points per field (sum of I_j)
+    long long* d_rowoff = nullptr;   // [J] first point of row j within a field
+    int* d_shape_of = nullptr;       // [Jh] shape index of latitude pair jh
+    RShape* d_shapes = nullptr;      // [nshapes]
+    void* d_twpass = nullptr;        // all shapes' per-pass twiddle tables
+    void* d_twpost = nullptr;        // all shapes' real-spectrum twiddles
+    int* d_rev = nullptr;            // all shapes' digit reversals
+    int nshapes = 0;
+};
+
 enum Stage { kStageFftFwd = 0, kStageLegFwd = 1, kStageLegInv = 2,
              kStageFftInv = 3, kStageSplitConv = 4 };
 
@@ -131,6 +153,7 @@ struct sht_plan_s {
     unsigned* d_colmax;        // FP16 split plans: [2][2F] column maxima (float bits)
                                // of the forward and inverse GEMMs' FP32 operand
     sht::Profiler* prof;       // per-launch timing, off by default
+    sht::RaggedGrid* ragged;   // reduced grid (per-latitude I_j); null: regular J x I
 };
 
 namespace sht {
@@ -152,6 +175,9 @@ cudaError_t build_node_tables(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_pnm_table(sht_plan_s* p, cudaStream_t s);
 cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
 cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
+cudaError_t build_fft_tables(const FftShape& sh, bool fp64, void* twpass, void* twpost,
+                             int* rev, void* tmp, cudaStream_t s);
+void ragged_free(RaggedGrid* rg);
 
 // Register DFT sizes of the two-pass FP32 FFT (L = Q x 32).
 __host__ __device__ constexpr bool fft_big_radix(int q) {

@@ -1,0 +1,276 @@
+// Reduced Clenshaw-Curtis grids: the Clenshaw-Curtis latitudes with a
+// longitude count I_j of their own on each latitude, as in the reduced and
+// octahedral grids Sec. 6 proposes for the Clenshaw-Curtis nodes.
+//
+// Sec. 6 quotes the reduction rule of the JMA model: latitude j needs at
+// least 4 M_j + 1 longitudes, M_j being the zonal wavenumber beyond which
+// every |P~_n^m(mu_j)| is below 1e-16.  sht_reduced_grid_sizes applies it
+// to a plan's P~ table: M_j = the largest m with some |P~_n^m(mu_j)| >=
+// 1e-16, and I_j = the smallest even count >= 4 M_j + 1 whose half has no
+// prime factor above 5, capped at the plan's I.
+//
+// A reduced plan is a Clenshaw-Curtis plan of I = max I_j whose FFT kernels
+// take, per latitude pair, the half-length L_j = I_j/2 and its tables.  Row
+// j of a field holds I_j points, rows packed one after another.  The
+// forward FFT of row j keeps the wavenumbers m <= min(N, L_j - 1) (the
+// Nyquist wavenumber L_j is not a mode of a real row) and writes zeros
+// above; the inverse synthesises the same range.  The weights of the
+// forward quadrature become w_j / I_j.  The Legendre contractions are those
+// of the full grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "sht_internal.h"
+
+namespace sht {
+namespace {
+
+// M_j for every northern node: thread per node, block row per m; a node
+// takes m if some n of that m is significant there.
+__global__ void latitude_mmax_kernel(const double* __restrict__ pnm, int ldp, int N, int Jh,
+                                     double thr, int* __restrict__ mmax) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    if (j >= Jh) return;
+    const size_t row0 = coef_offset(N, m);
+    bool sig = false;
+    for (int n = m; n <= N && !sig; ++n) sig = fabs(pnm[(row0 + (n - m)) * (size_t)ldp + j]) >= thr;
+    if (sig) atomicMax(&mmax[j], m);
+}
+
+bool smooth_half(int n) {
+    if (n < 2 || n % 2 != 0) return false;
+    int h = n / 2;
+    for (int p : {2, 3, 5})
+        while (h % p == 0) h /= p;
+    return h == 1;
+}
+
+int even_smooth_ceil(int x) {
+    int n = std::max(2, x);
+    while (!smooth_half(n)) ++n;
+    return n;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            switched = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+void ragged_free(RaggedGrid* rg) {
+    if (!rg) return;
+    void* ptrs[] = {rg->d_rowoff, rg->d_shape_of, rg->d_shapes, rg->d_twpass, rg->d_twpost,
+                    rg->d_rev};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete rg;
+}
+
+namespace {
+
+// Per-latitude tables of a reduced plan (I_lat already checked).
+int attach_ragged(sht_plan_s* p, const int* I_lat) {
+    const bool fp64 = p->prec == SHT_FP64;
+    const size_t vb = fp64 ? sizeof(double2) : sizeof(float2);
+    RaggedGrid* rg = new (std::nothrow) RaggedGrid();
+    if (!rg) {
+        set_error("host allocation failed");
+        return SHT_ERR_ALLOC;
+    }
+    rg->Ij.assign(I_lat, I_lat + p->J);
+    std::vector<long long> rowoff(p->J);
+    long long acc = 0;
+    for (int j = 0; j < p->J; ++j) {
+        rowoff[j] = acc;
+        acc += rg->Ij[j];
+    }
+    rg->npts = acc;
+    // distinct half-lengths, in order of first appearance from the pole
+    std::map<int, int> id;
+    std::vector<RShape> shapes;
+    std::vector<int> shape_of(p->Jh);
+    long long tw_total = 0, post_total = 0;
+    int Lmax = 1;
+    for (int jh = 0; jh < p->Jh; ++jh) {
+        const int L = rg->Ij[jh] / 2;
+        auto it = id.find(L);
+        if (it == id.end()) {
+            RShape r;
+            r.sh = fft_factor(L, fp64);
+            r.sh.L = L;
+            r.tw_off = tw_total;
+            r.post_off = post_total;
+            r.rev_off = post_total;
+            tw_total += std::max(r.sh.twtotal, 1);
+            post_total += L;
+            it = id.emplace(L, (int)shapes.size()).first;
+            shapes.push_back(r);
+            Lmax = std::max(Lmax, L);
+        }
+        shape_of[jh] = it->second;
+    }
+    rg->nshapes = (int)shapes.size();
+    void* tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** q, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(q, bytes);
+        if (e != cudaSuccess) *q = nullptr;
+    };
+    alloc((void**)&rg->d_rowoff, p->J * sizeof(long long));
+    alloc((void**)&rg->d_shape_of, p->Jh * sizeof(int));
+    alloc((void**)&rg->d_shapes, shapes.size() * sizeof(RShape));
+    alloc(&rg->d_twpass, tw_total * vb);
+    alloc(&rg->d_twpost, post_total * vb);
+    alloc((void**)&rg->d_rev, post_total * sizeof(int));
+    alloc(&tmp, Lmax * vb);
+    cudaStream_t s = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (size_t k = 0; k < shapes.size() && e == cudaSuccess; ++k) {
+        const RShape& r = shapes[k];
+        e = build_fft_tables(r.sh, fp64, static_cast<char*>(rg->d_twpass) + r.tw_off * vb,
+                             static_cast<char*>(rg->d_twpost) + r.post_off * vb,
+                             rg->d_rev + r.rev_off, tmp, s);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rg->d_rowoff, rowoff.data(), p->J * sizeof(long long),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rg->d_shape_of, shape_of.data(), p->Jh * sizeof(int),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rg->d_shapes, shapes.data(), shapes.size() * sizeof(RShape),
+                            cudaMemcpyHostToDevice, s);
+    // forward weights w_j / I_j (the discretised Eq. dFT of row j carries 1/I_j)
+    std::vector<double> w(p->Jh);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(w.data(), p->d_w, p->Jh * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        for (int jh = 0; jh < p->Jh; ++jh) w[jh] /= (double)rg->Ij[jh];
+        e = cudaMemcpyAsync(p->d_w_over_I, w.data(), p->Jh * sizeof(double),
+                            cudaMemcpyHostToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (s) cudaStreamDestroy(s);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        ragged_free(rg);
+        cudaGetLastError();
+        set_error("reduced-grid tables: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SHT_ERR_ALLOC : SHT_ERR_CUDA;
+    }
+    p->ragged = rg;
+    return SHT_OK;
+}
+
+}  // namespace
+}  // namespace sht
+
+using namespace sht;
+
+extern "C" int sht_reduced_grid_sizes(sht_plan_t p, int* I_lat) {
+    if (!p || !plan_is_live(p)) {
+        set_error("invalid or destroyed plan handle");
+        return SHT_ERR_HANDLE;
+    }
+    if (!I_lat) {
+        set_error("I_lat is NULL");
+        return SHT_ERR_ARG;
+    }
+    DeviceGuard dg(p->device);
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, p->Jh * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, p->Jh * sizeof(int));
+    if (e == cudaSuccess) {
+        const dim3 grid((p->Jh + 127) / 128, p->N + 1);
+        latitude_mmax_kernel<<<grid, 128>>>(p->d_pnm, p->ldp, p->N, p->Jh, 1e-16, d);
+        e = cudaGetLastError();
+    }
+    std::vector<int> mmax(p->Jh, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mmax.data(), d, p->Jh * sizeof(int), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("reduced-grid sizes: %s", cudaGetErrorString(e));
+        return SHT_ERR_CUDA;
+    }
+    for (int jh = 0; jh < p->Jh; ++jh) {
+        const int n = std::min(p->I, even_smooth_ceil(4 * mmax[jh] + 1));
+        I_lat[jh] = n;
+        I_lat[p->J - 1 - jh] = n;
+    }
+    return SHT_OK;
+}
+
+extern "C" int sht_plan_create_reduced(int N, int J, const int* I_lat, int nfields,
+                                       int precision, sht_plan_t* out) {
+    if (!out) {
+        set_error("out is NULL");
+        return SHT_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!I_lat) {
+        set_error("I_lat is NULL");
+        return SHT_ERR_ARG;
+    }
+    if (J < 1 || J % 2 == 0) {
+        set_error("J = %d must be odd and >= 1 (the Equator node is needed)", J);
+        return SHT_ERR_ARG;
+    }
+    int Imax = 0;
+    for (int j = 0; j < J; ++j) {
+        const int n = I_lat[j];
+        if (n < 2 || n > kMaxI || !smooth_half(n)) {
+            set_error("I_lat[%d] = %d must be even, <= %d, with I/2 a product of 2, 3 and 5",
+                      j, n, kMaxI);
+            return SHT_ERR_ARG;
+        }
+        if (n != I_lat[J - 1 - j]) {
+            set_error("I_lat must be symmetric about the Equator (I_lat[%d] = %d, I_lat[%d] = %d)",
+                      j, n, J - 1 - j, I_lat[J - 1 - j]);
+            return SHT_ERR_ARG;
+        }
+        Imax = std::max(Imax, n);
+    }
+    sht_plan_t p = nullptr;
+    const int rc = sht_plan_create_grid(N, J, Imax, nfields, precision, SHT_GRID_CC, &p);
+    if (rc < 0) return rc;
+    int rc2;
+    {
+        DeviceGuard dg(p->device);
+        rc2 = attach_ragged(p, I_lat);
+    }
+    if (rc2 != SHT_OK) {
+        sht_plan_destroy(p);
+        return rc2;
+    }
+    *out = p;
+    return rc;
+}
+
+extern "C" int sht_plan_grid_points(sht_plan_t p, long long* npts) {
+    if (!p || !plan_is_live(p)) {
+        set_error("invalid or destroyed plan handle");
+        return SHT_ERR_HANDLE;
+    }
+    if (!npts) {
+        set_error("npts is NULL");
+        return SHT_ERR_ARG;
+    }
+    *npts = p->ragged ? p->ragged->npts : (long long)p->J * p->I;
+    return SHT_OK;
+}

@@ -228,6 +228,46 @@ cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s) {
     return cudaStreamSynchronize(s);
 }
 
+// FFT tables of one half-length (I = 2 sh.L longitudes) into caller-owned
+// device buffers: the per-pass twiddle tables (sh.twtotal entries), the
+// real-spectrum twiddles e^{-2 pi i q / I} (L entries) and the digit-
+// reversed positions (L ints).  tmp holds L complex entries (the length-L
+// table the per-pass tables are gathered from).  Synchronises s.
+cudaError_t build_fft_tables(const FftShape& sh, bool fp64, void* twpass, void* twpost,
+                             int* rev, void* tmp, cudaStream_t s) {
+    const int L = sh.L;
+    const int threads = 128;
+    const int blocks = (L + threads - 1) / threads;
+    const int tblocks = (sh.twtotal + threads - 1) / threads;
+    if (fp64) {
+        twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)tmp, L, L);
+        if (sh.twtotal > 0)
+            twpass_kernel<double2><<<tblocks, threads, 0, s>>>((const double2*)tmp, sh,
+                                                               (double2*)twpass);
+        twiddle_kernel<double2><<<blocks, threads, 0, s>>>((double2*)twpost, L, 2 * L);
+    } else {
+        twiddle_kernel<float2><<<blocks, threads, 0, s>>>((float2*)tmp, L, L);
+        if (sh.twtotal > 0)
+            twpass_kernel<float2><<<tblocks, threads, 0, s>>>((const float2*)tmp, sh,
+                                                              (float2*)twpass);
+        twiddle_kernel<float2><<<blocks, threads, 0, s>>>((float2*)twpost, L, 2 * L);
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    std::vector<int> h(L);
+    for (int k = 0; k < L; ++k) {
+        int kk = k, pos = 0;
+        for (int q = 0; q < sh.npass; ++q) {
+            pos += (kk % sh.radix[q]) * sh.span[q];
+            kk /= sh.radix[q];
+        }
+        h[k] = pos;
+    }
+    err = cudaMemcpyAsync(rev, h.data(), L * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (err != cudaSuccess) return err;
+    return cudaStreamSynchronize(s);
+}
+
 }  // namespace sht
 
 namespace sht {

@@ -128,8 +128,8 @@ extern "C" int sht_inject_nested(sht_plan_t p, const void* fine_grid, int k, voi
         set_error("NULL buffer");
         return SHT_ERR_ARG;
     }
-    if (p->grid != SHT_GRID_CC) {
-        set_error("the shifted (Fejer first-rule) grid does not nest (Sec. 3.3)");
+    if (p->grid != SHT_GRID_CC || p->ragged) {
+        set_error("the shifted (Fejer first-rule) grid and reduced grids do not nest");
         return SHT_ERR_NOT_NESTED;
     }
     if (k < 1 || k > 8) {

@@ -18,19 +18,25 @@ def _stream_ptr(device):
 
 class Plan:
     """Spherical-harmonic transform plan on the J x I Clenshaw-Curtis grid
-    (``grid="cc"``) or on the shifted grid of Fejer's first rule
-    (``grid="fejer1"``, Sec. 3.3).
+    (``grid="cc"``), on the shifted grid of Fejer's first rule
+    (``grid="fejer1"``, Sec. 3.3), or on a reduced Clenshaw-Curtis grid
+    (``grid="reduced"``) with ``lat_points[j]`` longitudes on latitude j
+    (I is then ignored; see ``reduced_grid_sizes``).
 
-    Layouts: grid ``[nfields, J, I]`` real; spectrum ``[ncoef, nfields]``
-    complex (packed m-major, m >= 0 only).  ``precision`` is one of "fp64",
+    Layouts: grid ``[nfields, J, I]`` real (reduced: ``[nfields, sum of
+    lat_points]``, rows packed); spectrum ``[ncoef, nfields]`` complex
+    (packed m-major, m >= 0 only).  ``precision`` is one of "fp64",
     "bf16x2", "bf16x3", "fp16x2", "fp16x3"; FP64 plans use float64/complex128
     tensors, split plans float32/complex64."""
 
-    def __init__(self, N, J, I, nfields, precision="fp64", device=None, grid="cc"):
+    def __init__(self, N, J, I, nfields, precision="fp64", device=None, grid="cc",
+                 lat_points=None):
         if precision not in PRECISION:
             raise ValueError("precision must be one of %s" % list(PRECISION))
-        if grid not in _native.GRID:
-            raise ValueError("grid must be one of %s" % list(_native.GRID))
+        if grid not in _native.GRID and grid != "reduced":
+            raise ValueError("grid must be one of %s" % (list(_native.GRID) + ["reduced"]))
+        if (grid == "reduced") != (lat_points is not None):
+            raise ValueError("lat_points goes with grid='reduced' and only with it")
         self.grid = grid
         self.device = torch.device("cuda", torch.cuda.current_device()
                                    if device is None else torch.device(device).index or 0)
@@ -41,10 +47,26 @@ class Plan:
         self.ncoef = (N + 1) * (N + 2) // 2
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            rc = check(lib.sht_plan_create_grid(N, J, I, nfields, PRECISION[precision],
-                                                _native.GRID[grid], ctypes.byref(h)))
+            if grid == "reduced":
+                pts = [int(v) for v in lat_points]
+                if len(pts) != J:
+                    raise ValueError("lat_points needs J = %d entries" % J)
+                arr = (ctypes.c_int * J)(*pts)
+                rc = check(lib.sht_plan_create_reduced(N, J, arr, nfields,
+                                                       PRECISION[precision], ctypes.byref(h)))
+                self.lat_points = pts
+                self.I = max(pts)
+            else:
+                rc = check(lib.sht_plan_create_grid(N, J, I, nfields, PRECISION[precision],
+                                                    _native.GRID[grid], ctypes.byref(h)))
+                self.lat_points = None
         self.exact = rc == _native.SHT_OK
         self._h = h
+        npts = ctypes.c_longlong()
+        check(lib.sht_plan_grid_points(h, ctypes.byref(npts)))
+        self.npts = npts.value
+        self.grid_shape = ((self.F, self.npts) if grid == "reduced"
+                           else (self.F, self.J, self.I))
 
     # -- buffers ----------------------------------------------------------
     def _check(self, t, shape, dtype, name):
@@ -57,8 +79,7 @@ class Plan:
             raise ValueError("%s must be contiguous" % name)
 
     def empty_grid(self):
-        return torch.empty((self.F, self.J, self.I), dtype=self.real_dtype,
-                           device=self.device)
+        return torch.empty(self.grid_shape, dtype=self.real_dtype, device=self.device)
 
     def empty_spec(self):
         return torch.empty((self.ncoef, self.F), dtype=self.complex_dtype,
@@ -66,8 +87,8 @@ class Plan:
 
     # -- transforms -----------------------------------------------------------
     def forward(self, grid, out=None):
-        """Analysis: grid [F, J, I] -> spectrum [ncoef, F]."""
-        self._check(grid, (self.F, self.J, self.I), self.real_dtype, "grid")
+        """Analysis: grid (``grid_shape``) -> spectrum [ncoef, F]."""
+        self._check(grid, self.grid_shape, self.real_dtype, "grid")
         out = self.empty_spec() if out is None else out
         self._check(out, (self.ncoef, self.F), self.complex_dtype, "spec")
         check(lib.sht_forward(self._h, ctypes.c_void_p(grid.data_ptr()),
@@ -76,10 +97,10 @@ class Plan:
         return out
 
     def inverse(self, spec, out=None):
-        """Synthesis: spectrum [ncoef, F] -> grid [F, J, I]."""
+        """Synthesis: spectrum [ncoef, F] -> grid (``grid_shape``)."""
         self._check(spec, (self.ncoef, self.F), self.complex_dtype, "spec")
         out = self.empty_grid() if out is None else out
-        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        self._check(out, self.grid_shape, self.real_dtype, "grid")
         check(lib.sht_inverse(self._h, ctypes.c_void_p(spec.data_ptr()),
                               ctypes.c_void_p(out.data_ptr()),
                               _stream_ptr(self.device)))
@@ -91,9 +112,9 @@ class Plan:
         if which == 0:
             self._check(x, (self.ncoef, self.F), self.complex_dtype, "spec")
             out = self.empty_grid() if out is None else out
-            self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+            self._check(out, self.grid_shape, self.real_dtype, "grid")
         elif which == 1:
-            self._check(x, (self.F, self.J, self.I), self.real_dtype, "grid")
+            self._check(x, self.grid_shape, self.real_dtype, "grid")
             out = self.empty_spec() if out is None else out
             self._check(out, (self.ncoef, self.F), self.complex_dtype, "spec")
         else:
@@ -120,7 +141,7 @@ class Plan:
         self._check(coarse_spec, ((Nc + 1) * (Nc + 2) // 2, self.F), self.complex_dtype,
                     "coarse_spec")
         out = self.empty_grid() if out is None else out
-        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        self._check(out, self.grid_shape, self.real_dtype, "grid")
         check(lib.sht_prolong_spectral(self._h, ctypes.c_void_p(coarse_spec.data_ptr()), Nc,
                                        ctypes.c_void_p(out.data_ptr()),
                                        _stream_ptr(self.device)))
@@ -132,11 +153,19 @@ class Plan:
         Jf, If = 2 ** k * (self.J + 1) - 1, 2 ** k * self.I
         self._check(fine_grid, (self.F, Jf, If), self.real_dtype, "fine_grid")
         out = self.empty_grid() if out is None else out
-        self._check(out, (self.F, self.J, self.I), self.real_dtype, "grid")
+        self._check(out, self.grid_shape, self.real_dtype, "grid")
         check(lib.sht_inject_nested(self._h, ctypes.c_void_p(fine_grid.data_ptr()), k,
                                     ctypes.c_void_p(out.data_ptr()),
                                     _stream_ptr(self.device)))
         return out
+
+    def reduced_grid_sizes(self):
+        """Longitudes per latitude (J ints) of the reduced grid that the
+        1e-16 reduction rule of Sec. 6 gives on this plan's latitudes, capped
+        at its I (see ``sht_reduced_grid_sizes``)."""
+        out = (ctypes.c_int * self.J)()
+        check(lib.sht_reduced_grid_sizes(self._h, out))
+        return list(out)
 
     def tables(self):
         """(w [J], mu [J], pnm [ncoef, (J+1)/2]) copied from the device."""
