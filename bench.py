@@ -39,9 +39,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", default="T639")
-    ap.add_argument("--grid", default="cc", choices=["cc", "fejer1"],
-                    help="latitude grid: Clenshaw-Curtis or the shifted grid of "
+    ap.add_argument("--grid", default="cc", choices=["cc", "fejer1", "reduced"],
+                    help="latitude grid: Clenshaw-Curtis, the reduced Clenshaw-Curtis "
+                         "grid of the 1e-16 reduction rule (Sec. 6), or the shifted grid of "
                          "Fejer's first rule")
+    ap.add_argument("--reduced-rule", default="fast", choices=["fast", "smooth"],
+                    help="longitude counts of --grid reduced: lengths with compile-time "
+                         "FFT kernels (fast) or any 2-3-5-smooth count (smooth)")
     ap.add_argument("--precision", default="auto",
                     help="auto (headline path), fp64, bf16x3, ...")
     ap.add_argument("--fields", type=int, default=0,
@@ -164,10 +168,12 @@ def legendre_flops(w, F):
     return 2.0 * ncoef * Jh * 2 * F
 
 
-def fft_bytes(w, F, real_bytes):
-    """Grid read (or written) once + Fourier workspace written (or read) once."""
+def fft_bytes(w, F, real_bytes, npts=None):
+    """Grid read (or written) once + Fourier workspace written (or read) once;
+    npts: grid points per field (default J I; fewer on a reduced grid)."""
     Jh = (w.J + 1) // 2
-    return F * w.J * w.I * real_bytes + (w.N + 1) * 2 * Jh * F * 2 * real_bytes
+    npts = w.J * w.I if npts is None else npts
+    return F * npts * real_bytes + (w.N + 1) * 2 * Jh * F * 2 * real_bytes
 
 
 # DRAM traffic per launch of the kernels that dominate a step, from ncu
@@ -300,7 +306,7 @@ def split_gemm_bytes(w, F, prec, inverse):
     return (spec + tab + work)
 
 
-def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
+def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src, npts=None, grid="cc"):
     per_launch_s = tot_ms / n / 1000.0
     real_bytes = 8 if prec == "fp64" else 4
     if name.startswith("legendre") and prec == "fp64":
@@ -332,7 +338,7 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
                     "peak_source": "%s bf16_tflops_sustained" % pk_src,
                     "hbm_frac": h_frac}
     else:
-        b = fft_bytes(w, F, real_bytes)
+        b = fft_bytes(w, F, real_bytes, npts)
         if prec == "fp64":
             roof = {"kernel": name + "_f64", "bound": "alu",
                     "achieved": b / per_launch_s / 1e9, "peak": None,
@@ -346,7 +352,7 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
     if roof["peak"]:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["ms_per_launch"] = 1000 * per_launch_s
-    t = MEASURED_TRAFFIC.get((name, prec, w.name, F))
+    t = MEASURED_TRAFFIC.get((name, prec, w.name, F)) if grid != "reduced" else None
     if t is not None:
         roof["traffic"] = t
         roof["traffic_note"] = ("ncu DRAM bytes of the T639 x 64 capture scaled by the "
@@ -358,7 +364,15 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src):
 def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     import torch
     from paper_1711_11296_gb300 import sht, workloads as W
-    plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid=args.grid)
+    if args.grid == "reduced":
+        # longitudes per latitude by the reduction rule, from an FP64 plan's
+        # P~ table (plan setup, untimed)
+        sizes = sht.Plan(w.N, w.J, w.I, 1, "fp64",
+                         device=device).reduced_grid_sizes(args.reduced_rule)
+        plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid="reduced",
+                        lat_points=sizes)
+    else:
+        plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid=args.grid)
     if args.reduced:
         plan.set_reduced(True)
     # launch shapes picked by the library's autotuner (plan setup, untimed)
@@ -398,7 +412,7 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     ms_local = ev0.elapsed_time(ev1)
     barrier(dist, local)
     ms = max_over_ranks(dist, ms_local, device)
-    res = {"ms": ms, "prof": prof, "clocks": clocks,
+    res = {"ms": ms, "prof": prof, "clocks": clocks, "npts": plan.npts,
            "launches": sum(n for _, n in prof.values()),
            "tuning": {k: v for k, v in tuning.items() if k != "ms_per_pair"}}
 
@@ -482,9 +496,11 @@ def native_arm(args):
     value = job_throughput(world, F, args.steps, head["ms"])
     prof = head["prof"]
     name, (tot_ms, n) = max(prof.items(), key=lambda kv: kv[1][0])
-    roof = roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src)
+    npts = head["npts"]
+    roof = roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src, npts, args.grid)
     stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
-                  "roofline": roofline_for(k, v[0], v[1], w, F, prec, pk, pk_src)}
+                  "roofline": roofline_for(k, v[0], v[1], w, F, prec, pk, pk_src, npts,
+                                           args.grid)}
               for k, v in prof.items()}
 
     other = None
@@ -497,12 +513,14 @@ def native_arm(args):
         other = {"path": "fp64", "steps": a64.steps,
                  "value": job_throughput(world, F, a64.steps, r64["ms"]),
                  "ms_per_step": r64["ms"] / a64.steps,
-                 "roofline": roofline_for(n64, t64, c64, w, F, "fp64", pk, pk_src),
+                 "roofline": roofline_for(n64, t64, c64, w, F, "fp64", pk, pk_src, npts,
+                                          args.grid),
                  "gpu_launches": r64["launches"]}
         other["split_speedup"] = value / other["value"]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # (the oracle sample times the full grid; a reduced grid has no CPU leg)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.grid != "reduced":
         cpu = cpu_baseline(w)
 
     if rank == 0:
@@ -515,11 +533,13 @@ def native_arm(args):
             "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "J": w.J, "I": w.I,
                        "field_levels_per_gpu": F, "path": prec, "grid": args.grid,
+                       "grid_points_per_field": npts,
+                       "reduced_rule": args.reduced_rule if args.grid == "reduced" else None,
                        "reduced_transform": bool(args.reduced),
                        "parallelism": "replicas" if world > 1 else "single",
                        "launch_shapes": head.get("tuning"),
                        "l2": "inputs larger than L2 (grid %.1f GB)"
-                             % (F * w.J * w.I * (8 if prec == "fp64" else 4) / 1e9)},
+                             % (F * npts * (8 if prec == "fp64" else 4) / 1e9)},
             "roofline": dict(roof, note=("algorithmic work of the full transform; the "
                                          "reduced transform skips part of it")
                              if args.reduced else roof.get("note")),

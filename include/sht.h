@@ -273,9 +273,13 @@ int sht_plan_set_reduced(sht_plan_t plan, int on);
  * sht_reduced_grid_sizes applies the reduction rule Sec. 6 quotes (at
  * least 4 M_j + 1 longitudes, M_j the zonal wavenumber beyond which every
  * |P~_n^m(mu_j)| is below 1e-16) to any plan's P~ table: M_j = the largest
- * m with some |P~_n^m(mu_j)| >= 1e-16, and I_lat[j] = the smallest even
- * count >= 4 M_j + 1 whose half has no prime factor above 5, capped at the
- * plan's I.  I_lat: host array of J ints, written.  Synchronous.
+ * m with some |P~_n^m(mu_j)| >= 1e-16, and I_lat[j] = the smallest count
+ * >= 4 M_j + 1 allowed by `rule`, capped at the plan's I.  SHT_REDUCED_SMOOTH
+ * allows every even count whose half has no prime factor above 5 (fewest
+ * points); SHT_REDUCED_FAST allows the counts 2 L whose half-length L has a
+ * compile-time FFT kernel (128, 256, 512, 640, 1024, 1280, 2048, 2560):
+ * a few more points, far faster FFTs.  I_lat: host array of J ints,
+ * written.  SHT_ERR_ARG for an unknown rule.  Synchronous.
  *
  * sht_plan_create_reduced creates a plan on the Clenshaw-Curtis latitudes
  * of J nodes with I_lat[j] longitudes on latitude j (host array of J ints,
@@ -296,7 +300,8 @@ int sht_plan_set_reduced(sht_plan_t plan, int on);
  *
  * sht_plan_grid_points writes the points per field of any plan's grid
  * (sum_j I_lat[j] for a reduced plan, J I otherwise). */
-int sht_reduced_grid_sizes(sht_plan_t plan, int* I_lat);
+typedef enum { SHT_REDUCED_SMOOTH = 0, SHT_REDUCED_FAST = 1 } sht_reduced_rule;
+int sht_reduced_grid_sizes(sht_plan_t plan, int rule, int* I_lat);
 int sht_plan_create_reduced(int N, int J, const int* I_lat, int nfields, int precision,
                             sht_plan_t* out);
 int sht_plan_grid_points(sht_plan_t plan, long long* npts);

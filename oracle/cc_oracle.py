@@ -442,23 +442,28 @@ def _even_smooth_ceil(x):
         n += 1
 
 
-def reduced_sizes(N, J, I, thr=1e-16):
+def reduced_sizes(N, J, I, thr=1e-16, counts=None):
     """Longitude counts I_j of the reduced Clenshaw-Curtis grid.
 
     Sec. 6 quotes the reduction rule of the JMA model: latitude j carries at
     least 4 M_j + 1 longitudes, M_j being the zonal wavenumber beyond which
     every |P~_n^m(mu_j)| (0 <= n <= N) is below 1e-16.  Read here as:
     M_j = the largest m with some |P~_n^m(mu_j)| >= 1e-16, and I_j = the
-    smallest even 2-3-5-smooth count >= 4 M_j + 1, capped at the full grid's
-    I.  Returns (I_j [J], M_j [J]) with j = 1 first; the P~ come from the
-    binary128 recurrence rounded to FP64."""
+    smallest even 2-3-5-smooth count >= 4 M_j + 1 (or, if ``counts`` is
+    given, the smallest of those counts >= 4 M_j + 1, else I), capped at the
+    full grid's I.  Returns (I_j [J], M_j [J]) with j = 1 first; the P~ come
+    from the binary128 recurrence rounded to FP64."""
     P = pnm_cc(N, J)                                   # [ncoef][J]
     M = np.zeros(J, dtype=np.int64)
     for m in range(N + 1):
         r0 = coef_offset(N, m)
         sig = np.any(np.abs(P[r0:r0 + N - m + 1]) >= thr, axis=0)
         M[sig] = m
-    Ij = np.array([min(I, _even_smooth_ceil(4 * int(Mj) + 1)) for Mj in M], dtype=np.int64)
+    def pick(need):
+        if counts is None:
+            return _even_smooth_ceil(need)
+        return next((c for c in sorted(counts) if c >= need), I)
+    Ij = np.array([min(I, pick(4 * int(Mj) + 1)) for Mj in M], dtype=np.int64)
     return Ij, M
 
 

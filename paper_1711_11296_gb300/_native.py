@@ -35,6 +35,7 @@ STATUS = {
 }
 PRECISION = {"fp64": 0, "bf16x2": 1, "bf16x3": 2, "fp16x2": 3, "fp16x3": 4}
 GRID = {"cc": 0, "fejer1": 1}
+REDUCED_RULE = {"smooth": 0, "fast": 1}
 
 
 class SHTError(RuntimeError):
@@ -76,7 +77,7 @@ def _load():
     lib.sht_plan_set_tuning.argtypes = [vp, i, i]
     lib.sht_plan_get_tuning.argtypes = [vp, ip, ip]
     lib.sht_plan_autotune.argtypes = [vp, i, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]
-    lib.sht_reduced_grid_sizes.argtypes = [vp, ip]
+    lib.sht_reduced_grid_sizes.argtypes = [vp, i, ip]
     lib.sht_plan_create_reduced.argtypes = [i, i, ip, i, i, ctypes.POINTER(vp)]
     lib.sht_plan_grid_points.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.sht_last_error.restype = ctypes.c_char_p

@@ -34,6 +34,7 @@
 #include <math.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "sht_internal.h"
 
@@ -450,6 +451,7 @@ struct FwdArgs {
     double mscale0, mscale1;
     unsigned* colmax;   // FP16 split plans: max |output| per real column (float bits)
     const long long* rowoff;   // reduced grid: first point of each row (null: regular)
+    const int* jh_list;        // latitude pair of each CTA row (null: blockIdx.y)
     int F, J, Jh, L, LP, N, G;
     FftShape shape;
 };
@@ -466,6 +468,7 @@ struct InvArgs {
     double mfactor1;
     const long long* rowoff;   // reduced grid: first point of each row (null: regular)
     long long fstride;         // reduced grid: points per field
+    const int* jh_list;        // latitude pair of each CTA row (null: blockIdx.y)
     int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
@@ -540,7 +543,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     auto row_ptr = [&](int r) -> const T* {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
-        if (LT == 0 && A.rowoff) return A.grid + (long long)f * A.src.field_stride + A.rowoff[j];
+        if (A.rowoff) return A.grid + (long long)f * A.src.field_stride + A.rowoff[j];
         return A.grid + (long long)f * A.src.field_stride + A.src.row_offset +
                (long long)j * A.src.row_stride;
     };
@@ -649,66 +652,73 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     // output scales, converted once (FP64 conversions use the narrow FP64 pipe)
     const T sc0 = (T)0.5 * rs * (T)A.mscale0, sc1 = (T)0.5 * rs * (T)A.mscale1;
     // two outputs (m, fl) per iteration, idx and idx + NT, with all shared-
-    // memory reads of both issued before any arithmetic
-    // A reduced-grid row of half-length L carries the wavenumbers up to
-    // min(N, L - 1); those above are written as zeros (computed at the
-    // clamped wavenumber, then discarded).
-    const int kmax = (LT == 0 && A.rowoff) ? min(A.N, L - 1) : A.N;
-    auto clampk = [&](int m) -> int {
-        if constexpr (LT > 0)
-            return m;
-        else
-            return min(m, kmax);
+    // memory reads of both issued before any arithmetic.  A reduced-grid row
+    // of half-length L carries the wavenumbers up to min(N, L - 1); those
+    // above are written as zeros (computed at the clamped wavenumber, then
+    // discarded).  The loop is compiled twice, with and without that clamp.
+    const int kmax = A.rowoff ? min(A.N, L - 1) : A.N;
+    auto out_loop = [&](auto rag) {
+        constexpr bool RAG = decltype(rag)::value;
+        auto clampk = [&](int m) -> int {
+            if constexpr (RAG)
+                return min(m, kmax);
+            else
+                return m;
+        };
+        Walk2 wa(tid, nf), wb(tid + NT, nf);
+        for (; wa.major * nf + wa.minor < nout; wa.next(), wa.next(), wb.next(), wb.next()) {
+            const bool hb = wb.major * nf + wb.minor < nout;
+            const int ma = wa.major, fa = wa.minor;
+            const int mb = hb ? wb.major : ma, fb = hb ? wb.minor : fa;
+            const int ra = clampk(ma), rb = clampk(mb);
+            const int pma = ph<T>(rev_of<T, LT>(ra, A.rev));
+            const int pca = ph<T>(rev_of<T, LT>(ra == 0 ? 0 : L - ra, A.rev));
+            const int pmb = ph<T>(rev_of<T, LT>(rb, A.rev));
+            const int pcb = ph<T>(rev_of<T, LT>(rb == 0 ? 0 : L - rb, A.rev));
+            const V* na = rows + (size_t)fa * LP;
+            const V* nb = rows + (size_t)fb * LP;
+            const V a_nm = na[pma], a_nc = na[pca], b_nm = nb[pmb], b_nc = nb[pcb];
+            V a_sm = K::make((T)0, (T)0), a_sc = a_sm, b_sm = a_sm, b_sc = a_sm;
+            if (!equator) {
+                const V* sa = na + (size_t)nf * LP;
+                const V* sb = nb + (size_t)nf * LP;
+                a_sm = sa[pma];
+                a_sc = sa[pca];
+                b_sm = sb[pmb];
+                b_sc = sb[pcb];
+            }
+            const V wta = A.twpost[ra], wtb = A.twpost[rb];
+            const T sca = ma == 0 ? sc0 : sc1;
+            const T scb = mb == 0 ? sc0 : sc1;
+            const V xan = real_spec(a_nm, a_nc, wta), xbn = real_spec(b_nm, b_nc, wtb);
+            V Sa = xan, Aa = K::make((T)0, (T)0), Sb = xbn, Ab = Aa;
+            if (!equator) {
+                const V xas = real_spec(a_sm, a_sc, wta), xbs = real_spec(b_sm, b_sc, wtb);
+                Sa = K::add(xan, xas);
+                Aa = K::sub(xan, xas);
+                Sb = K::add(xbn, xbs);
+                Ab = K::sub(xbn, xbs);
+            }
+            V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
+            if (ra != ma) osa = oaa = K::make((T)0, (T)0);
+            const size_t basea = ((size_t)ma * 2 * A.Jh + jh) * A.F + f0 + fa;
+            A.work[basea] = osa;
+            A.work[basea + (size_t)A.Jh * A.F] = oaa;
+            if (track) record(fa, osa, oaa);
+            if (hb) {
+                V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
+                if (rb != mb) osb = oab = K::make((T)0, (T)0);
+                const size_t baseb = ((size_t)mb * 2 * A.Jh + jh) * A.F + f0 + fb;
+                A.work[baseb] = osb;
+                A.work[baseb + (size_t)A.Jh * A.F] = oab;
+                if (track) record(fb, osb, oab);
+            }
+        }
     };
-    Walk2 wa(tid, nf), wb(tid + NT, nf);
-    for (; wa.major * nf + wa.minor < nout; wa.next(), wa.next(), wb.next(), wb.next()) {
-        const bool hb = wb.major * nf + wb.minor < nout;
-        const int ma = wa.major, fa = wa.minor;
-        const int mb = hb ? wb.major : ma, fb = hb ? wb.minor : fa;
-        const int ra = clampk(ma), rb = clampk(mb);
-        const int pma = ph<T>(rev_of<T, LT>(ra, A.rev));
-        const int pca = ph<T>(rev_of<T, LT>(ra == 0 ? 0 : L - ra, A.rev));
-        const int pmb = ph<T>(rev_of<T, LT>(rb, A.rev));
-        const int pcb = ph<T>(rev_of<T, LT>(rb == 0 ? 0 : L - rb, A.rev));
-        const V* na = rows + (size_t)fa * LP;
-        const V* nb = rows + (size_t)fb * LP;
-        const V a_nm = na[pma], a_nc = na[pca], b_nm = nb[pmb], b_nc = nb[pcb];
-        V a_sm = K::make((T)0, (T)0), a_sc = a_sm, b_sm = a_sm, b_sc = a_sm;
-        if (!equator) {
-            const V* sa = na + (size_t)nf * LP;
-            const V* sb = nb + (size_t)nf * LP;
-            a_sm = sa[pma];
-            a_sc = sa[pca];
-            b_sm = sb[pmb];
-            b_sc = sb[pcb];
-        }
-        const V wta = A.twpost[ra], wtb = A.twpost[rb];
-        const T sca = ma == 0 ? sc0 : sc1;
-        const T scb = mb == 0 ? sc0 : sc1;
-        const V xan = real_spec(a_nm, a_nc, wta), xbn = real_spec(b_nm, b_nc, wtb);
-        V Sa = xan, Aa = K::make((T)0, (T)0), Sb = xbn, Ab = Aa;
-        if (!equator) {
-            const V xas = real_spec(a_sm, a_sc, wta), xbs = real_spec(b_sm, b_sc, wtb);
-            Sa = K::add(xan, xas);
-            Aa = K::sub(xan, xas);
-            Sb = K::add(xbn, xbs);
-            Ab = K::sub(xbn, xbs);
-        }
-        V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
-        if (ra != ma) osa = oaa = K::make((T)0, (T)0);
-        const size_t basea = ((size_t)ma * 2 * A.Jh + jh) * A.F + f0 + fa;
-        A.work[basea] = osa;
-        A.work[basea + (size_t)A.Jh * A.F] = oaa;
-        if (track) record(fa, osa, oaa);
-        if (hb) {
-            V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
-            if (rb != mb) osb = oab = K::make((T)0, (T)0);
-            const size_t baseb = ((size_t)mb * 2 * A.Jh + jh) * A.F + f0 + fb;
-            A.work[baseb] = osb;
-            A.work[baseb + (size_t)A.Jh * A.F] = oab;
-            if (track) record(fb, osb, oab);
-        }
-    }
+    if (LT == 0 || A.rowoff)
+        out_loop(std::true_type{});
+    else
+        out_loop(std::false_type{});
     if (track) {
         flush();
         __syncthreads();
@@ -719,7 +729,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
 template <typename T, int LT, bool STRIDED>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_forward_kernel(const __grid_constant__ FwdArgs<T> A) {
-    fwd_body<T, LT, STRIDED>(A, blockIdx.x, blockIdx.y);
+    fwd_body<T, LT, STRIDED>(A, blockIdx.x, A.jh_list ? A.jh_list[blockIdx.y] : blockIdx.y);
 }
 
 template <typename T, int LT>
@@ -760,7 +770,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
     // asynchronously; then both hemispheres are formed in place)
     // a reduced-grid row of half-length L carries the wavenumbers up to
     // min(N, L - 1) (Y_m = 0 above)
-    const int kmax = (LT == 0 && A.rowoff) ? min(A.N, L - 1) : A.N;
+    const int kmax = A.rowoff ? min(A.N, L - 1) : A.N;
     const int nin = (kmax + 1) * nf;
     for (Walk2 w(tid, nf); w.major * nf + w.minor < nin; w.next()) {
         const int m = w.major, fl = w.minor;
@@ -833,7 +843,9 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
             const int r = idx / Q, b = idx - r * Q;
             const int f = f0 + (r < nf ? r : r - nf);
             const int j = (r < nf) ? jh : (A.J - 1 - jh);
-            V* xv = reinterpret_cast<V*>(A.grid + ((long long)f * A.J + j) * A.I) + b;
+            V* xv = reinterpret_cast<V*>(
+                        A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
+                                 : A.grid + ((long long)f * A.J + j) * A.I) + b;
             const V* zb = rows + (size_t)r * LP + ph<T>(b * R);
             V a[R];
 #pragma unroll
@@ -850,8 +862,8 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
         V* xv = reinterpret_cast<V*>(
-            (LT == 0 && A.rowoff) ? A.grid + (long long)f * A.fstride + A.rowoff[j]
-                                  : A.grid + ((long long)f * A.J + j) * A.I);
+            A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
+                     : A.grid + ((long long)f * A.J + j) * A.I);
         const V* z = rows + (size_t)r * LP;
         if constexpr (LT > 0) {
             // all of the thread's shared-memory reads of the row first
@@ -879,7 +891,7 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
 template <typename T, int LT>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_inverse_kernel(const __grid_constant__ InvArgs<T> A) {
-    inv_body<T, LT>(A, blockIdx.x, blockIdx.y);
+    inv_body<T, LT>(A, blockIdx.x, A.jh_list ? A.jh_list[blockIdx.y] : blockIdx.y);
 }
 
 // ---- grouped launches: several plans' rows in one grid ----------------
@@ -936,7 +948,7 @@ template <typename T> struct RaggedInv {
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_forward_ragged_kernel(const __grid_constant__ RaggedFwd<T> R) {
-    const int jh = blockIdx.y;
+    const int jh = R.a.jh_list[blockIdx.y];
     const RShape& rs = R.shapes[R.shape_of[jh]];
     FwdArgs<T> A = R.a;
     A.shape = rs.sh;
@@ -950,7 +962,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_inverse_ragged_kernel(const __grid_constant__ RaggedInv<T> R) {
-    const int jh = blockIdx.y;
+    const int jh = R.a.jh_list[blockIdx.y];
     const RShape& rs = R.shapes[R.shape_of[jh]];
     InvArgs<T> A = R.a;
     A.shape = rs.sh;
@@ -1013,6 +1025,7 @@ FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource&
     A.mscale1 = sc.mscale1;
     A.colmax = p->d_colmax;
     A.rowoff = nullptr;
+    A.jh_list = nullptr;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
@@ -1048,6 +1061,7 @@ InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& 
     A.mfactor1 = sc.mfactor1;
     A.rowoff = nullptr;
     A.fstride = (long long)p->J * p->I;
+    A.jh_list = nullptr;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
@@ -1065,32 +1079,88 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
 #undef SHT_INV
 }
 
+// Dispatch of a compile-time length (the lengths of fft_has_fixed_kernel).
+#define SHT_FFT_FIXED(L, CALL)                       \
+    switch (L) {                                     \
+        case 64: return CALL(64);                    \
+        case 128: return CALL(128);                  \
+        case 256: return CALL(256);                  \
+        case 320: return CALL(320);                  \
+        case 512: return CALL(512);                  \
+        case 640: return CALL(640);                  \
+        case 1024: return CALL(1024);                \
+        case 1280: return CALL(1280);                \
+        default: return cudaErrorInvalidValue;       \
+    }
+
+// Arguments of one length class of a reduced grid: that shape's tables and
+// row pitch, and the class's latitude-pair list.
+template <typename Args>
+void set_class(Args& A, const RaggedGrid* rg, const RShape& r, int off, size_t vb) {
+    using V = std::remove_cv_t<std::remove_pointer_t<decltype(A.twp)>>;
+    A.L = r.sh.L;
+    A.shape = r.sh;
+    A.LP = fft_row_pitch(r.sh.L, vb == 16);
+    A.twp = reinterpret_cast<const V*>(static_cast<const char*>(rg->d_twpass) + r.tw_off * vb);
+    A.twpost = reinterpret_cast<const V*>(static_cast<const char*>(rg->d_twpost) + r.post_off * vb);
+    A.rev = rg->d_rev + r.rev_off;
+    A.jh_list = rg->d_jh + off;
+}
+
+template <typename T>
+cudaError_t fwd_ragged_class(const FwdArgs<T>& A, dim3 g, size_t smem, cudaStream_t s) {
+#define SHT_FWDC(LV) fwd_launch<T, LV>(A, false, g, smem, s)
+    SHT_FFT_FIXED(A.L, SHT_FWDC)
+#undef SHT_FWDC
+}
+
+template <typename T>
+cudaError_t inv_ragged_class(const InvArgs<T>& A, dim3 g, size_t smem, cudaStream_t s) {
+#define SHT_INVC(LV) inv_launch<T, LV>(A, g, smem, s)
+    SHT_FFT_FIXED(A.L, SHT_INVC)
+#undef SHT_INVC
+}
+
+// Reduced grid: one launch of the compile-time kernel per length class that
+// has one, then one launch of the generic kernel (a shape per CTA) over the
+// remaining latitude pairs.
 template <typename T>
 cudaError_t fwd_ragged_impl(const sht_plan_s* p, const void* grid, const FwdScale& sc,
                             void* work, cudaStream_t s) {
     using V = typename Vec2<T>::type;
     const RaggedGrid* rg = p->ragged;
+    const size_t vb = sizeof(V);
     RowSource src;
     src.field_stride = rg->npts;
     src.row_stride = 0;
     src.row_offset = 0;
     src.elem_stride = 1;
+    FwdArgs<T> base = make_fwd_args<T>(p, grid, src, sc, work);
+    base.rowoff = rg->d_rowoff;
+    if (base.colmax) {
+        const cudaError_t e = cudaMemsetAsync(base.colmax, 0, 2 * (size_t)p->F * sizeof(unsigned), s);
+        if (e) return e;
+    }
+    const unsigned nfg = (p->F + p->G - 1) / p->G;
+    for (const auto& c : rg->classes) {
+        FwdArgs<T> A = base;
+        set_class(A, rg, rg->h_shapes[c.shape], c.off, vb);
+        const cudaError_t e = fwd_ragged_class<T>(A, dim3(nfg, c.count),
+                                                  fft_smem_bytes(2 * A.L, p->G, vb == 16), s);
+        if (e) return e;
+    }
+    if (rg->generic_count == 0) return cudaSuccess;
     RaggedFwd<T> R;
-    R.a = make_fwd_args<T>(p, grid, src, sc, work);
-    R.a.rowoff = rg->d_rowoff;
+    R.a = base;
     R.a.twp = static_cast<const V*>(rg->d_twpass);
     R.a.twpost = static_cast<const V*>(rg->d_twpost);
     R.a.rev = rg->d_rev;
+    R.a.jh_list = rg->d_jh + rg->generic_off;
     R.shapes = rg->d_shapes;
     R.shape_of = rg->d_shape_of;
-    if (R.a.colmax) {
-        const cudaError_t e = cudaMemsetAsync(R.a.colmax, 0, 2 * (size_t)p->F * sizeof(unsigned), s);
-        if (e) return e;
-    }
     cudaError_t e = ensure_smem((const void*)fft_forward_ragged_kernel<T>, p->fft_smem);
     if (e) return e;
-    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
-    fft_forward_ragged_kernel<T><<<g, NT, p->fft_smem, s>>>(R);
+    fft_forward_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
     return cudaGetLastError();
 }
 
@@ -1099,19 +1169,30 @@ cudaError_t inv_ragged_impl(const sht_plan_s* p, const void* work, const InvScal
                             void* grid, cudaStream_t s) {
     using V = typename Vec2<T>::type;
     const RaggedGrid* rg = p->ragged;
+    const size_t vb = sizeof(V);
+    InvArgs<T> base = make_inv_args<T>(p, work, sc, grid);
+    base.rowoff = rg->d_rowoff;
+    base.fstride = rg->npts;
+    const unsigned nfg = (p->F + p->G - 1) / p->G;
+    for (const auto& c : rg->classes) {
+        InvArgs<T> A = base;
+        set_class(A, rg, rg->h_shapes[c.shape], c.off, vb);
+        const cudaError_t e = inv_ragged_class<T>(A, dim3(nfg, c.count),
+                                                  fft_smem_bytes(2 * A.L, p->G, vb == 16), s);
+        if (e) return e;
+    }
+    if (rg->generic_count == 0) return cudaSuccess;
     RaggedInv<T> R;
-    R.a = make_inv_args<T>(p, work, sc, grid);
-    R.a.rowoff = rg->d_rowoff;
-    R.a.fstride = rg->npts;
+    R.a = base;
     R.a.twp = static_cast<const V*>(rg->d_twpass);
     R.a.twpost = static_cast<const V*>(rg->d_twpost);
     R.a.rev = rg->d_rev;
+    R.a.jh_list = rg->d_jh + rg->generic_off;
     R.shapes = rg->d_shapes;
     R.shape_of = rg->d_shape_of;
     cudaError_t e = ensure_smem((const void*)fft_inverse_ragged_kernel<T>, p->fft_smem);
     if (e) return e;
-    const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
-    fft_inverse_ragged_kernel<T><<<g, NT, p->fft_smem, s>>>(R);
+    fft_inverse_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,20 @@ struct RaggedGrid {
     void* d_twpost = nullptr;        // all shapes' real-spectrum twiddles
     int* d_rev = nullptr;            // all shapes' digit reversals
     int nshapes = 0;
+    // Latitude pairs by launch: one launch per half-length that has a
+    // compile-time FFT kernel (classes), one generic launch for the rest.
+    struct Class { int shape; int off; int count; };
+    std::vector<Class> classes;
+    std::vector<RShape> h_shapes;    // host copy of d_shapes
+    int generic_off = 0, generic_count = 0;
+    int* d_jh = nullptr;             // latitude-pair lists of all launches
 };
+
+// Half-lengths with compile-time FFT kernels (the standard grids).
+inline bool fft_has_fixed_kernel(int L) {
+    return L == 64 || L == 128 || L == 256 || L == 320 || L == 512 || L == 640 || L == 1024 ||
+           L == 1280;
+}
 
 enum Stage { kStageFftFwd = 0, kStageLegFwd = 1, kStageLegInv = 2,
              kStageFftInv = 3, kStageSplitConv = 4 };

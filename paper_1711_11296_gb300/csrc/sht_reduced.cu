@@ -7,7 +7,9 @@
 // every |P~_n^m(mu_j)| is below 1e-16.  sht_reduced_grid_sizes applies it
 // to a plan's P~ table: M_j = the largest m with some |P~_n^m(mu_j)| >=
 // 1e-16, and I_j = the smallest even count >= 4 M_j + 1 whose half has no
-// prime factor above 5, capped at the plan's I.
+// prime factor above 5 (SHT_REDUCED_SMOOTH), or whose half is one of the
+// lengths with a compile-time FFT kernel (SHT_REDUCED_FAST: fewer distinct
+// lengths, a few more points), capped at the plan's I.
 //
 // A reduced plan is a Clenshaw-Curtis plan of I = max I_j whose FFT kernels
 // take, per latitude pair, the half-length L_j = I_j/2 and its tables.  Row
@@ -73,7 +75,7 @@ struct DeviceGuard {
 void ragged_free(RaggedGrid* rg) {
     if (!rg) return;
     void* ptrs[] = {rg->d_rowoff, rg->d_shape_of, rg->d_shapes, rg->d_twpass, rg->d_twpost,
-                    rg->d_rev};
+                    rg->d_rev, rg->d_jh};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete rg;
@@ -123,6 +125,21 @@ int attach_ragged(sht_plan_s* p, const int* I_lat) {
         shape_of[jh] = it->second;
     }
     rg->nshapes = (int)shapes.size();
+    rg->h_shapes = shapes;
+    // launch lists: latitude pairs of each compile-time length, then the rest
+    std::vector<int> jh_all;
+    for (int k = 0; k < rg->nshapes; ++k) {
+        if (!fft_has_fixed_kernel(shapes[k].sh.L)) continue;
+        RaggedGrid::Class c{k, (int)jh_all.size(), 0};
+        for (int jh = 0; jh < p->Jh; ++jh)
+            if (shape_of[jh] == k) jh_all.push_back(jh);
+        c.count = (int)jh_all.size() - c.off;
+        rg->classes.push_back(c);
+    }
+    rg->generic_off = (int)jh_all.size();
+    for (int jh = 0; jh < p->Jh; ++jh)
+        if (!fft_has_fixed_kernel(shapes[shape_of[jh]].sh.L)) jh_all.push_back(jh);
+    rg->generic_count = (int)jh_all.size() - rg->generic_off;
     void* tmp = nullptr;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** q, size_t bytes) {
@@ -135,6 +152,7 @@ int attach_ragged(sht_plan_s* p, const int* I_lat) {
     alloc(&rg->d_twpass, tw_total * vb);
     alloc(&rg->d_twpost, post_total * vb);
     alloc((void**)&rg->d_rev, post_total * sizeof(int));
+    alloc((void**)&rg->d_jh, jh_all.size() * sizeof(int));
     alloc(&tmp, Lmax * vb);
     cudaStream_t s = nullptr;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -152,6 +170,9 @@ int attach_ragged(sht_plan_s* p, const int* I_lat) {
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(rg->d_shapes, shapes.data(), shapes.size() * sizeof(RShape),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rg->d_jh, jh_all.data(), jh_all.size() * sizeof(int),
                             cudaMemcpyHostToDevice, s);
     // forward weights w_j / I_j (the discretised Eq. dFT of row j carries 1/I_j)
     std::vector<double> w(p->Jh);
@@ -181,13 +202,17 @@ int attach_ragged(sht_plan_s* p, const int* I_lat) {
 
 using namespace sht;
 
-extern "C" int sht_reduced_grid_sizes(sht_plan_t p, int* I_lat) {
+extern "C" int sht_reduced_grid_sizes(sht_plan_t p, int rule, int* I_lat) {
     if (!p || !plan_is_live(p)) {
         set_error("invalid or destroyed plan handle");
         return SHT_ERR_HANDLE;
     }
     if (!I_lat) {
         set_error("I_lat is NULL");
+        return SHT_ERR_ARG;
+    }
+    if (rule != SHT_REDUCED_SMOOTH && rule != SHT_REDUCED_FAST) {
+        set_error("unknown reduction rule %d", rule);
         return SHT_ERR_ARG;
     }
     DeviceGuard dg(p->device);
@@ -209,7 +234,17 @@ extern "C" int sht_reduced_grid_sizes(sht_plan_t p, int* I_lat) {
         return SHT_ERR_CUDA;
     }
     for (int jh = 0; jh < p->Jh; ++jh) {
-        const int n = std::min(p->I, even_smooth_ceil(4 * mmax[jh] + 1));
+        const int need = 4 * mmax[jh] + 1;
+        int n = even_smooth_ceil(need);
+        if (rule == SHT_REDUCED_FAST) {
+            n = p->I;
+            for (int L : {64, 128, 256, 320, 512, 640, 1024, 1280})
+                if (2 * L >= need) {
+                    n = 2 * L;
+                    break;
+                }
+        }
+        n = std::min(p->I, n);
         I_lat[jh] = n;
         I_lat[p->J - 1 - jh] = n;
     }

@@ -159,12 +159,15 @@ class Plan:
                                     _stream_ptr(self.device)))
         return out
 
-    def reduced_grid_sizes(self):
+    def reduced_grid_sizes(self, rule="smooth"):
         """Longitudes per latitude (J ints) of the reduced grid that the
         1e-16 reduction rule of Sec. 6 gives on this plan's latitudes, capped
-        at its I (see ``sht_reduced_grid_sizes``)."""
+        at its I.  ``rule``: "smooth" (any even 2-3-5-smooth count) or "fast"
+        (counts with compile-time FFT kernels); see ``sht_reduced_grid_sizes``."""
+        if rule not in _native.REDUCED_RULE:
+            raise ValueError("rule must be one of %s" % list(_native.REDUCED_RULE))
         out = (ctypes.c_int * self.J)()
-        check(lib.sht_reduced_grid_sizes(self._h, out))
+        check(lib.sht_reduced_grid_sizes(self._h, _native.REDUCED_RULE[rule], out))
         return list(out)
 
     def tables(self):

@@ -15,6 +15,8 @@ from sht_testutil import assert_fp64_close, built_lib, rel_l2, to_cuda
 pytestmark = pytest.mark.gpu
 
 SPLIT_TOL = {"bf16x3": 1e-6, "fp16x2": 2e-6}
+# longitude counts whose half-length has a compile-time FFT kernel
+FAST_COUNTS = [128, 256, 512, 640, 1024, 1280, 2048, 2560]
 
 
 @pytest.fixture(scope="module")
@@ -24,9 +26,9 @@ def sht():
     return S
 
 
-def _rule(sht, N, J, I):
+def _rule(sht, N, J, I, rule="smooth"):
     full = sht.Plan(N, J, I, 1, "fp64")
-    return full.reduced_grid_sizes()
+    return full.reduced_grid_sizes(rule)
 
 
 def _hand_grid(J, I):
@@ -39,16 +41,18 @@ def _hand_grid(J, I):
     return pts
 
 
+@pytest.mark.parametrize("rule", ["smooth", "fast"])
 @pytest.mark.parametrize("N,J,I", [(31, 65, 128), (63, 129, 256), (159, 321, 640)])
-def test_sizes_match_oracle(sht, N, J, I):
-    got = _rule(sht, N, J, I)
-    want, _ = O.reduced_sizes(N, J, I)
+def test_sizes_match_oracle(sht, rule, N, J, I):
+    got = _rule(sht, N, J, I, rule)
+    want, _ = O.reduced_sizes(N, J, I, counts=FAST_COUNTS if rule == "fast" else None)
     assert got == [int(v) for v in want]
 
 
+@pytest.mark.parametrize("rule", ["smooth", "fast"])
 @pytest.mark.parametrize("N,J,I,F", [(31, 65, 128, 3), (63, 129, 256, 2)])
-def test_fp64_rule_grid_matches_oracle(sht, N, J, I, F):
-    pts = _rule(sht, N, J, I)
+def test_fp64_rule_grid_matches_oracle(sht, rule, N, J, I, F):
+    pts = _rule(sht, N, J, I, rule)
     p = sht.Plan(N, J, I, F, "fp64", grid="reduced", lat_points=pts)
     assert p.npts == sum(pts) and p.grid_shape == (F, sum(pts))
     a = W.random_spectrum(N, F, "n^-1.5", seed=1800 + N)
@@ -78,10 +82,14 @@ def test_fp64_hand_grid_cuts_the_spectrum(sht):
     p.status()
 
 
+@pytest.mark.parametrize("rule", ["smooth", "fast"])
 @pytest.mark.parametrize("prec", ["bf16x3", "fp16x2"])
 @pytest.mark.parametrize("N,J,I,F", [(63, 129, 256, 5), (159, 321, 640, 4)])
-def test_split_rule_grid_matches_oracle(sht, prec, N, J, I, F):
-    pts = _rule(sht, N, J, I)
+def test_split_rule_grid_matches_oracle(sht, rule, prec, N, J, I, F):
+    # the fast rule's rows all run compile-time kernels (at T159 the
+    # register-fed first and last passes of L = 256 and 320 included); the
+    # smooth rule's mix them with the generic kernel
+    pts = _rule(sht, N, J, I, rule)
     p = sht.Plan(N, J, I, F, prec, grid="reduced", lat_points=pts)
     x = W.random_grid(F, 1, sum(pts), seed=1820 + N)[:, 0, :]
     x = x.astype(np.float32).astype(np.float64)
@@ -146,3 +154,5 @@ def test_rejected_requests(sht):
     assert ei.value.code == -7
     with pytest.raises(ValueError):
         sht.Plan(N, J, I, 1, "fp64", lat_points=pts)
+    with pytest.raises(ValueError):
+        sht.Plan(N, J, I, 1, "fp64").reduced_grid_sizes("octahedral")
