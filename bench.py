@@ -404,7 +404,8 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     plan.profile(False)
-    prof = plan.profile_read()
+    prof3 = plan.profile_read(kernels=True)
+    prof = {k: (v[0], v[1]) for k, v in prof3.items()}
     plan.status()
     # NaN/Inf guard: a step that produced non-finite output is not a result
     if not bool(torch.isfinite(torch.view_as_real(spec_out)).all()):
@@ -413,7 +414,8 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted):
     barrier(dist, local)
     ms = max_over_ranks(dist, ms_local, device)
     res = {"ms": ms, "prof": prof, "clocks": clocks, "npts": plan.npts,
-           "launches": sum(n for _, n in prof.values()),
+           "launches": sum(v[2] for v in prof3.values()),
+           "kernels": {k: v[2] for k, v in prof3.items()},
            "tuning": {k: v for k, v in tuning.items() if k != "ms_per_pair"}}
 
     if e2e_wanted:
@@ -499,6 +501,7 @@ def native_arm(args):
     npts = head["npts"]
     roof = roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src, npts, args.grid)
     stages = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1],
+                  "kernels": head["kernels"].get(k),
                   "roofline": roofline_for(k, v[0], v[1], w, F, prec, pk, pk_src, npts,
                                            args.grid)}
               for k, v in prof.items()}

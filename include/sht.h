@@ -318,12 +318,19 @@ int sht_plan_copy_tables(sht_plan_t plan, double* w, double* mu, double* pnm);
 int sht_profile_enable(sht_plan_t plan, int on);
 
 /* Synchronise the recorded events and return, per stage, the summed device
- * time in milliseconds and the number of launches since the last read,
- * then reset.  ms and launches are host arrays of SHT_PROFILE_STAGES
- * entries: 0 forward FFT (+fold), 1 forward Legendre, 2 inverse Legendre,
- * 3 inverse FFT (+unfold), 4 split-precision operand conversion. */
+ * time in milliseconds and the number of times the stage ran since the
+ * last read, then reset.  ms and launches are host arrays of
+ * SHT_PROFILE_STAGES entries: 0 forward FFT (+fold), 1 forward Legendre,
+ * 2 inverse Legendre, 3 inverse FFT (+unfold), 4 split-precision operand
+ * conversion.  sht_profile_read_kernels also writes, per stage, the number
+ * of kernels the library launched inside it (kernels: host array of
+ * SHT_PROFILE_STAGES entries, or NULL): a stage can be several kernels,
+ * e.g. the spectrum split and the GEMM of the split inverse Legendre
+ * contraction, or one launch per row length on a reduced grid. */
 #define SHT_PROFILE_STAGES 8
 int sht_profile_read(sht_plan_t plan, double* ms, long long* launches);
+int sht_profile_read_kernels(sht_plan_t plan, double* ms, long long* launches,
+                             long long* kernels);
 
 /* Message of the last error on this thread ("" if none). */
 const char* sht_last_error(void);

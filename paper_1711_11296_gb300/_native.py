@@ -20,7 +20,7 @@ EXPORTED = [
     "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
     "sht_plan_create_grid", "sht_plan_set_reduced", "sht_prolong_spectral",
     "sht_inject_nested", "sht_reduced_grid_sizes", "sht_plan_create_reduced",
-    "sht_plan_grid_points",
+    "sht_plan_grid_points", "sht_profile_read_kernels",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -67,6 +67,8 @@ def _load():
     lib.sht_plan_copy_tables.argtypes = [vp, dp, dp, dp]
     lib.sht_profile_enable.argtypes = [vp, i]
     lib.sht_profile_read.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+    lib.sht_profile_read_kernels.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_longlong)]
     lib.sht_forward_noalloc.argtypes = [i, i, i, i, vp, vp, vp]
     lib.sht_plan_status.argtypes = [vp]
     vpp = ctypes.POINTER(vp)

@@ -129,8 +129,10 @@ cudaEvent_t Profiler::get() {
     return e;
 }
 
+thread_local long long g_kernels = 0;
+
 ProfScope::ProfScope(const sht_plan_s* plan, int st, cudaStream_t stream)
-    : p(plan), stage(st), s(stream) {
+    : p(plan), stage(st), s(stream), k0(g_kernels) {
     if (p->prof && p->prof->on) {
         a = p->prof->get();
         if (a) cudaEventRecord(a, s);
@@ -145,7 +147,7 @@ ProfScope::~ProfScope() {
         return;
     }
     cudaEventRecord(b, s);
-    p->prof->recs.push_back({stage, a, b});
+    p->prof->recs.push_back({stage, a, b, g_kernels - k0});
 }
 
 }  // namespace sht
@@ -498,11 +500,16 @@ extern "C" int sht_profile_enable(sht_plan_t p, int on) {
     return SHT_OK;
 }
 
-extern "C" int sht_profile_read(sht_plan_t p, double* ms, long long* launches) {
+extern "C" int sht_profile_read_kernels(sht_plan_t p, double* ms, long long* launches,
+                                        long long* kernels) {
     int rc = check_plan(p);
     if (rc) return rc;
     if (!ms || !launches) { set_error("NULL output"); return SHT_ERR_ARG; }
-    for (int k = 0; k < SHT_PROFILE_STAGES; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (int k = 0; k < SHT_PROFILE_STAGES; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+        if (kernels) kernels[k] = 0;
+    }
     if (!p->prof) return SHT_OK;
     DeviceGuard dg(p->device);
     int status = SHT_OK;
@@ -514,12 +521,17 @@ extern "C" int sht_profile_read(sht_plan_t p, double* ms, long long* launches) {
         if (r.stage >= 0 && r.stage < SHT_PROFILE_STAGES) {
             ms[r.stage] += t;
             launches[r.stage] += 1;
+            if (kernels) kernels[r.stage] += r.kernels;
         }
         p->prof->pool.push_back(r.a);
         p->prof->pool.push_back(r.b);
     }
     p->prof->recs.clear();
     return status;
+}
+
+extern "C" int sht_profile_read(sht_plan_t p, double* ms, long long* launches) {
+    return sht_profile_read_kernels(p, ms, launches, nullptr);
 }
 
 extern "C" int sht_plan_status(sht_plan_t p) {

@@ -980,9 +980,11 @@ cudaError_t fwd_launch(const FwdArgs<T>& A, bool strided, dim3 grid, size_t smem
     if (!strided) {
         if ((e = ensure_smem((const void*)fft_forward_kernel<T, LT, false>, smem))) return e;
         fft_forward_kernel<T, LT, false><<<grid, NT, smem, s>>>(A);
+        note_launch();
     } else {
         if ((e = ensure_smem((const void*)fft_forward_kernel<T, LT, true>, smem))) return e;
         fft_forward_kernel<T, LT, true><<<grid, NT, smem, s>>>(A);
+        note_launch();
     }
     return cudaGetLastError();
 }
@@ -992,6 +994,7 @@ cudaError_t inv_launch(const InvArgs<T>& A, dim3 grid, size_t smem, cudaStream_t
     cudaError_t e = ensure_smem((const void*)fft_inverse_kernel<T, LT>, smem);
     if (e) return e;
     fft_inverse_kernel<T, LT><<<grid, NT, smem, s>>>(A);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1161,6 +1164,7 @@ cudaError_t fwd_ragged_impl(const sht_plan_s* p, const void* grid, const FwdScal
     cudaError_t e = ensure_smem((const void*)fft_forward_ragged_kernel<T>, p->fft_smem);
     if (e) return e;
     fft_forward_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1193,6 +1197,7 @@ cudaError_t inv_ragged_impl(const sht_plan_s* p, const void* work, const InvScal
     cudaError_t e = ensure_smem((const void*)fft_inverse_ragged_kernel<T>, p->fft_smem);
     if (e) return e;
     fft_inverse_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1224,6 +1229,7 @@ cudaError_t fwd_group_impl(sht_plan_s* const* plans, int n, const void* const* g
     cudaError_t e = ensure_smem((const void*)fft_forward_group_kernel<T>, smem);
     if (e) return e;
     fft_forward_group_kernel<T><<<G.cta_start[n], NT, smem, s>>>(G);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1245,6 +1251,7 @@ cudaError_t inv_group_impl(sht_plan_s* const* plans, int n, void* const* grids,
     cudaError_t e = ensure_smem((const void*)fft_inverse_group_kernel<T>, smem);
     if (e) return e;
     fft_inverse_group_kernel<T><<<G.cta_start[n], NT, smem, s>>>(G);
+    note_launch();
     return cudaGetLastError();
 }
 

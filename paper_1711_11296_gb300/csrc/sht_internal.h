@@ -115,7 +115,7 @@ enum Stage { kStageFftFwd = 0, kStageLegFwd = 1, kStageLegInv = 2,
 // Optional per-launch event timing.
 struct Profiler {
     bool on = false;
-    struct Rec { int stage; cudaEvent_t a, b; };
+    struct Rec { int stage; cudaEvent_t a, b; long long kernels; };
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
     cudaEvent_t get();
@@ -174,11 +174,18 @@ namespace sht {
 bool plan_is_live(const sht_plan_s* p);
 
 // Bracket a launch with profiling events when the plan's profiler is on.
+// Kernels the library has launched on this thread for transforms (every
+// per-call launch site calls note_launch); a profiling scope records how
+// many fell inside it.
+extern thread_local long long g_kernels;
+inline void note_launch() { ++g_kernels; }
+
 struct ProfScope {
     const sht_plan_s* p;
     int stage;
     cudaStream_t s;
     cudaEvent_t a = nullptr;
+    long long k0 = 0;
     ProfScope(const sht_plan_s* plan, int st, cudaStream_t stream);
     ~ProfScope();
 };

@@ -202,6 +202,7 @@ cudaError_t launch_legendre_fp64_group(sht_plan_s* const* plans, int n, bool inv
         legendre_inv_fp64_group_kernel<<<ntiles, NT, 0, s>>>(G, tiles);
     else
         legendre_fwd_fp64_group_kernel<<<ntiles, NT, 0, s>>>(G, tiles);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -229,6 +230,7 @@ cudaError_t launch_legendre_fwd_fp64(const sht_plan_s* p, const double* work,
     if (p->ntiles_fwd == 0) return cudaSuccess;
     legendre_fwd_fp64_kernel<<<p->ntiles_fwd, NT, 0, s>>>(
         p->d_pnm, p->ldp, work, spec, p->d_tiles_fwd, p->N, p->Jh, 2 * p->F, p->d_jmin);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -237,6 +239,7 @@ cudaError_t launch_legendre_inv_fp64(const sht_plan_s* p, const double* spec,
     if (p->ntiles_inv == 0) return cudaSuccess;
     legendre_inv_fp64_kernel<<<p->ntiles_inv, NT, 0, s>>>(
         p->d_pnm, p->ldp, spec, work, p->d_tiles_inv, p->N, p->Jh, 2 * p->F, p->d_jmin);
+    note_launch();
     return cudaGetLastError();
 }
 

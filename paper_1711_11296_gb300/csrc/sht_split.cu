@@ -933,6 +933,7 @@ cudaError_t launch_colmax_inverse(const sht_plan_s* p, const void* spec, cudaStr
     ry = std::min<long long>(ry, std::max<long long>(1, nrows / 64));
     colmax_kernel<<<dim3(cx, (unsigned)ry), dim3(32, 8), 0, s>>>(
         static_cast<const float*>(spec), nrows, C, p->N + 1, cm);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1032,6 +1033,7 @@ cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
     cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16, BPRE, TN>, smem);
     if (e) return e;
     split_gemm_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(g);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1076,6 +1078,7 @@ cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, void* 
     const Fn k = tab[(variant(st->terms, st->fp16, false, st->tn) & 3) | (st->tn == 64 ? 4 : 0)];
     k<<<grid, 256, smem, s>>>(B, st->d_probs_inv, C, nct, cm, st->inv_bplanes, pb, p->d_pnm,
                               p->ldp, p->N, p->Jh, O);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -1333,6 +1336,7 @@ cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
     cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16, BPRE, TN>, smem);
     if (e) return e;
     split_gemm_group_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(G);
+    note_launch();
     return cudaGetLastError();
 }
 

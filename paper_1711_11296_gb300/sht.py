@@ -220,12 +220,14 @@ class Plan:
         """Turn per-launch event timing on or off."""
         check(lib.sht_profile_enable(self._h, 1 if on else 0))
 
-    def profile_read(self):
-        """{stage: (total_ms, launches)} since the last read (synchronises)."""
+    def profile_read(self, kernels=False):
+        """{stage: (total_ms, runs)} since the last read (synchronises); with
+        kernels=True {stage: (total_ms, runs, kernels launched)}."""
         ms = (ctypes.c_double * _native.PROFILE_STAGES)()
         n = (ctypes.c_longlong * _native.PROFILE_STAGES)()
-        check(lib.sht_profile_read(self._h, ms, n))
-        return {_native.STAGE_NAMES[k]: (ms[k], n[k])
+        kn = (ctypes.c_longlong * _native.PROFILE_STAGES)()
+        check(lib.sht_profile_read_kernels(self._h, ms, n, kn))
+        return {_native.STAGE_NAMES[k]: ((ms[k], n[k], kn[k]) if kernels else (ms[k], n[k]))
                 for k in range(_native.PROFILE_STAGES) if n[k]}
 
     def close(self):
