@@ -163,6 +163,13 @@ int sht_restrict_nested(sht_plan_t coarse, const void* fine_grid, int k,
 int sht_prolong_spectral(sht_plan_t fine, const void* coarse_spec, int Nc, void* fine_grid,
                          void* stream);
 
+/* The same prolongation added onto fine_grid (fine_grid += synthesis of the
+ * zero-padded spectrum): the correction step of the two-grid V-cycle of
+ * Appendix C, fused into the inverse FFT's store.  Arguments and errors as
+ * sht_prolong_spectral; fine_grid is read and written. */
+int sht_prolong_spectral_add(sht_plan_t fine, const void* coarse_spec, int Nc,
+                             void* fine_grid, void* stream);
+
 /* Multigrid restriction in grid space by injection (Appendix C): the coarse
  * plan's grid is every 2^k-th latitude (j_f = 2^k (j+1) - 1, 0-based) and
  * every 2^k-th longitude of the fine grid [nfields][2^k (J+1) - 1][2^k I]

@@ -20,7 +20,7 @@ EXPORTED = [
     "sht_plan_set_tuning", "sht_plan_get_tuning", "sht_plan_autotune",
     "sht_plan_create_grid", "sht_plan_set_reduced", "sht_prolong_spectral",
     "sht_inject_nested", "sht_reduced_grid_sizes", "sht_plan_create_reduced",
-    "sht_plan_grid_points", "sht_profile_read_kernels",
+    "sht_plan_grid_points", "sht_profile_read_kernels", "sht_prolong_spectral_add",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -55,6 +55,7 @@ def _load():
     lib.sht_plan_create_grid.argtypes = [i, i, i, i, i, i, ctypes.POINTER(vp)]
     lib.sht_plan_set_reduced.argtypes = [vp, i]
     lib.sht_prolong_spectral.argtypes = [vp, vp, i, vp, vp]
+    lib.sht_prolong_spectral_add.argtypes = [vp, vp, i, vp, vp]
     lib.sht_inject_nested.argtypes = [vp, vp, i, vp, vp]
     lib.sht_plan_destroy.argtypes = [vp]
     lib.sht_plan_query.argtypes = [vp, ip, ip, ip, ip, ip, ip,

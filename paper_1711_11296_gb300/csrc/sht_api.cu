@@ -381,6 +381,17 @@ int inverse_impl(sht_plan_t p, const void* spec, const InvScale& sc, void* grid,
     return SHT_OK;
 }
 
+}  // namespace
+
+// The inverse path with the FFT's scaling and store mode given (used by the
+// multigrid prolongation, which can add onto the grid).
+int sht::inverse_scaled(sht_plan_t p, const void* spec, const InvScale& sc, void* grid,
+                        cudaStream_t s) {
+    return inverse_impl(p, spec, sc, grid, s);
+}
+
+namespace {
+
 RowSource plain_source(const sht_plan_s* p) {
     RowSource src;
     src.field_stride = (long long)p->J * p->I;

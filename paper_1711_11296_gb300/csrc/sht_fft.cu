@@ -469,6 +469,7 @@ struct InvArgs {
     const long long* rowoff;   // reduced grid: first point of each row (null: regular)
     long long fstride;         // reduced grid: points per field
     const int* jh_list;        // latitude pair of each CTA row (null: blockIdx.y)
+    int accumulate;            // 1: grid += rows (prolongation of a correction)
     int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
@@ -839,21 +840,35 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         constexpr int Q = FS.radix[0];   // index per butterfly
         passes_fixed<T, LT, 0, 1>(rows, nrows, LP, tws);
         const V sgn = K::make(rs, -rs);   // x = conj(z) rs
-        for (int idx = tid; idx < nrows * Q; idx += NT) {
-            const int r = idx / Q, b = idx - r * Q;
-            const int f = f0 + (r < nf ? r : r - nf);
-            const int j = (r < nf) ? jh : (A.J - 1 - jh);
-            V* xv = reinterpret_cast<V*>(
-                        A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
-                                 : A.grid + ((long long)f * A.J + j) * A.I) + b;
-            const V* zb = rows + (size_t)r * LP + ph<T>(b * R);
-            V a[R];
+        // compiled with and without accumulation into the grid
+        auto last_pass = [&](auto acc) {
+            constexpr bool ACC = decltype(acc)::value;
+            for (int idx = tid; idx < nrows * Q; idx += NT) {
+                const int r = idx / Q, b = idx - r * Q;
+                const int f = f0 + (r < nf ? r : r - nf);
+                const int j = (r < nf) ? jh : (A.J - 1 - jh);
+                V* xv = reinterpret_cast<V*>(
+                            A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
+                                     : A.grid + ((long long)f * A.J + j) * A.I) + b;
+                const V* zb = rows + (size_t)r * LP + ph<T>(b * R);
+                V a[R];
 #pragma unroll
-            for (int t = 0; t < R; ++t) a[t] = zb[t];
-            Dft<T, R>::run(a);
+                for (int t = 0; t < R; ++t) a[t] = zb[t];
+                Dft<T, R>::run(a);
 #pragma unroll
-            for (int k1 = 0; k1 < R; ++k1) xv[k1 * Q] = mul_f32x2(a[Dft<T, R>::pos(k1)], sgn);
-        }
+                for (int k1 = 0; k1 < R; ++k1) {
+                    const V y = mul_f32x2(a[Dft<T, R>::pos(k1)], sgn);
+                    if constexpr (ACC)
+                        xv[k1 * Q] = K::add(xv[k1 * Q], y);
+                    else
+                        xv[k1 * Q] = y;
+                }
+            }
+        };
+        if (A.accumulate)
+            last_pass(std::true_type{});
+        else
+            last_pass(std::false_type{});
         return;
     }
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
@@ -877,12 +892,16 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
 #pragma unroll
             for (int i = 0; i < NIT; ++i) {
                 const int k = tid + i * NT;
-                if (LT % NT == 0 || k < LT) xv[k] = K::make(v[i].x * rs, -v[i].y * rs);
+                if (LT % NT == 0 || k < LT) {
+                    const V y = K::make(v[i].x * rs, -v[i].y * rs);
+                    xv[k] = A.accumulate ? K::add(xv[k], y) : y;
+                }
             }
         } else {
             for (int k = tid; k < L; k += NT) {
                 const V v = z[ph<T>(rev_of<T, LT>(k, A.rev))];
-                xv[k] = K::make(v.x * rs, -v.y * rs);
+                const V y = K::make(v.x * rs, -v.y * rs);
+                xv[k] = A.accumulate ? K::add(xv[k], y) : y;
             }
         }
     }
@@ -1065,6 +1084,7 @@ InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& 
     A.rowoff = nullptr;
     A.fstride = (long long)p->J * p->I;
     A.jh_list = nullptr;
+    A.accumulate = sc.accumulate;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);

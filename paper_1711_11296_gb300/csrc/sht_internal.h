@@ -70,6 +70,7 @@ struct FwdScale {
 struct InvScale {
     const double* rowscale;   // [Jh] per northern row (w_j/I or 1), may be null
     double mfactor1;          // factor for m >= 1 before the Hermitian sum
+    int accumulate = 0;       // 1: add the rows to the grid instead of writing them
 };
 
 struct SplitTables;   // tensor-core operand tables (split plans)
@@ -198,6 +199,8 @@ cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
 cudaError_t build_fft_tables(const FftShape& sh, bool fp64, void* twpass, void* twpost,
                              int* rev, void* tmp, cudaStream_t s);
 void ragged_free(RaggedGrid* rg);
+int inverse_scaled(sht_plan_s* p, const void* spec, const InvScale& sc, void* grid,
+                   cudaStream_t s);
 
 // Register DFT sizes of the two-pass FP32 FFT (L = Q x 32).
 __host__ __device__ constexpr bool fft_big_radix(int q) {

@@ -3,7 +3,8 @@
 // spectrum (Sec. 3.2, sht_restrict_nested):
 //   * prolongation in spectral space: the lower-resolution spectral space is
 //     a subset of the higher one, so a spectrum truncated at Nc <= N is
-//     zero-padded to N and synthesised on the fine grid;
+//     zero-padded to N and synthesised on the fine grid, or added onto it
+//     (the V-cycle's correction step, fused into the inverse FFT's store);
 //   * restriction in grid space by injection: the coarse grid is every 2^k-th
 //     latitude (j_f = 2^k (j_c + 1) - 1, 0-based) and longitude of the fine
 //     grid.
@@ -77,8 +78,11 @@ int check(sht_plan_t p) {
 
 using namespace sht;
 
-extern "C" int sht_prolong_spectral(sht_plan_t p, const void* coarse_spec, int Nc,
-                                    void* fine_grid, void* stream) {
+namespace sht {
+namespace {
+
+int prolong(sht_plan_t p, const void* coarse_spec, int Nc, void* fine_grid, void* stream,
+            int accumulate) {
     int rc = check(p);
     if (rc) return rc;
     if (!coarse_spec || !fine_grid) {
@@ -117,7 +121,21 @@ extern "C" int sht_prolong_spectral(sht_plan_t p, const void* coarse_spec, int N
         set_error("zero-padding launch: %s", cudaGetErrorString(e));
         return SHT_ERR_CUDA;
     }
-    return sht_inverse(p, p->d_spec_pad, fine_grid, stream);
+    InvScale sc{nullptr, 1.0, accumulate};
+    return inverse_scaled(p, p->d_spec_pad, sc, fine_grid, s);
+}
+
+}  // namespace
+}  // namespace sht
+
+extern "C" int sht_prolong_spectral(sht_plan_t p, const void* coarse_spec, int Nc,
+                                    void* fine_grid, void* stream) {
+    return prolong(p, coarse_spec, Nc, fine_grid, stream, 0);
+}
+
+extern "C" int sht_prolong_spectral_add(sht_plan_t p, const void* coarse_spec, int Nc,
+                                        void* fine_grid, void* stream) {
+    return prolong(p, coarse_spec, Nc, fine_grid, stream, 1);
 }
 
 extern "C" int sht_inject_nested(sht_plan_t p, const void* fine_grid, int k, void* coarse_grid,

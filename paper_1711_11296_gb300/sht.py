@@ -135,16 +135,20 @@ class Plan:
                                       _stream_ptr(self.device)))
         return out
 
-    def prolong_spectral(self, coarse_spec, Nc, out=None):
+    def prolong_spectral(self, coarse_spec, Nc, out=None, add=False):
         """Grid of a spectrum truncated at Nc <= N, zero-padded to this plan's
-        N (multigrid prolongation in spectral space, Appendix C)."""
+        N (multigrid prolongation in spectral space, Appendix C).  With
+        add=True the grid is added onto ``out`` (required), the V-cycle's
+        correction step."""
         self._check(coarse_spec, ((Nc + 1) * (Nc + 2) // 2, self.F), self.complex_dtype,
                     "coarse_spec")
+        if add and out is None:
+            raise ValueError("add=True needs the grid to add onto (out)")
         out = self.empty_grid() if out is None else out
         self._check(out, self.grid_shape, self.real_dtype, "grid")
-        check(lib.sht_prolong_spectral(self._h, ctypes.c_void_p(coarse_spec.data_ptr()), Nc,
-                                       ctypes.c_void_p(out.data_ptr()),
-                                       _stream_ptr(self.device)))
+        fn = lib.sht_prolong_spectral_add if add else lib.sht_prolong_spectral
+        check(fn(self._h, ctypes.c_void_p(coarse_spec.data_ptr()), Nc,
+                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(self.device)))
         return out
 
     def inject_nested(self, fine_grid, k, out=None):

@@ -82,3 +82,48 @@ def test_transfer_argument_errors(sht):
     f1 = sht.Plan(*COARSE, 1, "fp64", grid="fejer1")
     with pytest.raises(sht.SHTError):
         f1.inject_nested(torch.zeros((1, 63, 64), dtype=torch.float64, device="cuda"), 1)
+
+
+# A fine grid whose FP32 FFT half-length (320 = 10 x 32) writes the grid
+# from its last pass, and the coarse grid it nests with k = 1.
+COARSE2 = (79, 159, 320)
+FINE2 = (159, 319, 640)
+
+
+@pytest.mark.parametrize("shapes", [(COARSE, FINE), (COARSE2, FINE2)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_prolong_add_is_grid_plus_prolongation(sht, prec, shapes):
+    # the accumulating store adds, in the plan's precision, exactly the
+    # values that the plain prolongation writes
+    (Nc, _, _), (N, J, I) = shapes
+    F = 3
+    p = sht.Plan(N, J, I, F, prec)
+    a = to_cuda(W.random_spectrum(Nc, F, "n^-1.5", seed=1830 + N), p.complex_dtype)
+    g0 = to_cuda(W.random_grid(F, J, I, seed=1831 + N), p.real_dtype)
+    out = g0.clone()
+    p.prolong_spectral(a, Nc, out=out, add=True)
+    assert torch.equal(out, g0 + p.prolong_spectral(a, Nc))
+    with pytest.raises(ValueError):
+        p.prolong_spectral(a, Nc, add=True)
+    p.status()
+
+
+@pytest.mark.parametrize("shapes", [(COARSE, FINE), (COARSE2, FINE2)])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_two_grid_correction_cancels_a_coarse_band_field(sht, prec, shapes):
+    # Appendix C's V-cycle transfers on a fine field band-limited to the
+    # coarse truncation: restricting it (Sec. 3.2, exact here) and adding
+    # back the prolongation of minus that spectrum leaves zero.
+    (Nc, Jc, Ic), (N, J, I) = shapes
+    F = 2
+    coarse = sht.Plan(Nc, Jc, Ic, F, prec)
+    fine = sht.Plan(N, J, I, F, prec)
+    a = W.random_spectrum(Nc, F, "n^-1.5", seed=1840 + N)
+    a[:Nc + 1] = a[:Nc + 1].real
+    x = fine.prolong_spectral(to_cuda(a, fine.complex_dtype), Nc)
+    scale = float(x.abs().max())
+    r = coarse.restrict_nested(x, 1)
+    fine.prolong_spectral(-r, Nc, out=x, add=True)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert float(x.abs().max()) <= tol * scale
+    fine.status()
