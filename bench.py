@@ -159,7 +159,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per launch (explained in the design doc)
+# algorithmic work per launch
 # ---------------------------------------------------------------------------
 def legendre_flops(w, F):
     """Folded contraction: 2 flops per (coefficient, northern node, real column)."""

@@ -68,7 +68,7 @@ typedef enum {
     SHT_ERR_NOT_NESTED = -4, /* grids do not nest (Sec. 3.2)                 */
     SHT_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up      */
     SHT_ERR_HANDLE = -6,     /* NULL, destroyed or foreign plan handle       */
-    SHT_ERR_UNSUPPORTED = -7 /* valid request this build does not implement  */
+    SHT_ERR_UNSUPPORTED = -7 /* valid request the library does not implement */
 } sht_status;
 
 /* Create a plan for truncation N on the J x I Clenshaw-Curtis grid with
