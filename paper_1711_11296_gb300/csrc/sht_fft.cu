@@ -329,8 +329,10 @@ __device__ __forceinline__ void bfly_fixed(typename Vec2<T>::type* z, int base,
 }
 
 // In-place mixed-radix DIF FFT over `nrows` padded rows (pitch LP), shape
-// known at run time.
-template <typename T>
+// known at run time.  BIG = false leaves out the two-pass radices above 8
+// (their shapes, L = Q x 32, all have compile-time kernels, so only the
+// grouped launches meet them at run time): far fewer registers.
+template <typename T, bool BIG = true>
 __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
                                const FftShape& sh, const typename Vec2<T>::type* twp) {
     const int L = sh.L;
@@ -348,7 +350,7 @@ __device__ void passes_runtime(typename Vec2<T>::type* rows, int nrows, int LP,
             const int n1 = b - blk * M;
             auto* z = rows + (size_t)row * LP;
             const int base = blk * S + n1;
-            if constexpr (sizeof(T) == 4) {   // two-pass shapes (FP32 only)
+            if constexpr (sizeof(T) == 4 && BIG) {   // two-pass shapes (FP32 only)
                 if (r > 8) {
                     if (r == 10) bfly<T, 10>(z, base, M, tw, n1);
                     else if (r == 16) bfly<T, 16>(z, base, M, tw, n1);
@@ -488,6 +490,8 @@ __device__ __forceinline__ void load_twiddles(V* dst, const V* src, int n) {
     for (int e = threadIdx.x; e < n; e += NT) dst[e] = src[e];
 }
 
+// LT > 0: the compile-time shape of that half-length; LT = 0: any shape at
+// run time; LT = -1: a run-time shape without the two-pass radices.
 template <typename T, int LT>
 __device__ __forceinline__ void run_passes(typename Vec2<T>::type* rows, int nrows, int LP,
                                            const FftShape& sh,
@@ -495,7 +499,7 @@ __device__ __forceinline__ void run_passes(typename Vec2<T>::type* rows, int nro
     if constexpr (LT > 0)
         passes_fixed<T, LT, 0>(rows, nrows, LP, twp);
     else
-        passes_runtime<T>(rows, nrows, LP, sh, twp);
+        passes_runtime<T, LT == 0>(rows, nrows, LP, sh, twp);
 }
 
 template <typename T, int LT>
@@ -716,7 +720,7 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             }
         }
     };
-    if (LT == 0 || A.rowoff)
+    if (LT <= 0 || A.rowoff)
         out_loop(std::true_type{});
     else
         out_loop(std::false_type{});
@@ -975,7 +979,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     A.twp += rs.tw_off;
     A.twpost += rs.post_off;
     A.rev += rs.rev_off;
-    fwd_body<T, 0, false>(A, blockIdx.x, jh);
+    fwd_body<T, -1, false>(A, blockIdx.x, jh);
 }
 
 template <typename T>
@@ -989,7 +993,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     A.twp += rs.tw_off;
     A.twpost += rs.post_off;
     A.rev += rs.rev_off;
-    inv_body<T, 0>(A, blockIdx.x, jh);
+    inv_body<T, -1>(A, blockIdx.x, jh);
 }
 
 template <typename T, int LT>
@@ -1028,8 +1032,16 @@ cudaError_t inv_launch(const InvArgs<T>& A, dim3 grid, size_t smem, cudaStream_t
         case 640: return CALL(640);        \
         case 1024: return CALL(1024);      \
         case 1280: return CALL(1280);      \
-        default: return CALL(0);           \
+        default: return CALL(-1);          \
     }
+
+// The run-time-shape kernels outside grouped launches (LT = -1) carry only
+// radices up to 8; every shape with a larger radix has a compile-time kernel.
+inline bool small_radices(const FftShape& sh) {
+    for (int q = 0; q < sh.npass; ++q)
+        if (sh.radix[q] > 8) return false;
+    return true;
+}
 
 template <typename T>
 FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource& src,
@@ -1064,6 +1076,7 @@ cudaError_t fwd_impl(const sht_plan_s* p, const void* grid, const RowSource& src
     }
     const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
     const bool strided = src.elem_stride != 1;
+    if (!fft_has_fixed_kernel(p->fft.L) && !small_radices(p->fft)) return cudaErrorInvalidValue;
 #define SHT_FWD(LV) fwd_launch<T, LV>(A, strided, g, p->fft_smem, s)
     SHT_FFT_DISPATCH(p->fft.L, SHT_FWD)
 #undef SHT_FWD
@@ -1097,6 +1110,7 @@ cudaError_t inv_impl(const sht_plan_s* p, const void* work, const InvScale& sc,
                      void* grid, cudaStream_t s) {
     const InvArgs<T> A = make_inv_args<T>(p, work, sc, grid);
     const dim3 g((p->F + p->G - 1) / p->G, p->Jh);
+    if (!fft_has_fixed_kernel(p->fft.L) && !small_radices(p->fft)) return cudaErrorInvalidValue;
 #define SHT_INV(LV) inv_launch<T, LV>(A, g, p->fft_smem, s)
     SHT_FFT_DISPATCH(p->fft.L, SHT_INV)
 #undef SHT_INV

@@ -140,6 +140,16 @@ int attach_ragged(sht_plan_s* p, const int* I_lat) {
     for (int jh = 0; jh < p->Jh; ++jh)
         if (!fft_has_fixed_kernel(shapes[shape_of[jh]].sh.L)) jh_all.push_back(jh);
     rg->generic_count = (int)jh_all.size() - rg->generic_off;
+    // the generic kernel carries radices up to 8 only (see fft_factor: the
+    // larger ones belong to the compile-time lengths)
+    for (const RShape& r : shapes)
+        if (!fft_has_fixed_kernel(r.sh.L))
+            for (int q = 0; q < r.sh.npass; ++q)
+                if (r.sh.radix[q] > 8) {
+                    delete rg;
+                    set_error("half-length %d needs radix %d", r.sh.L, r.sh.radix[q]);
+                    return SHT_ERR_UNSUPPORTED;
+                }
     void* tmp = nullptr;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** q, size_t bytes) {
