@@ -939,7 +939,20 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     int p = 0;
     while (p + 1 < G.n && b >= G.cta_start[p + 1]) ++p;
     const int local = b - G.cta_start[p];
-    fwd_body<T, 0, false>(G.a[p], local % G.nfg[p], local / G.nfg[p]);
+    const FwdArgs<T>& A = G.a[p];
+    const int fg = local % G.nfg[p], jh = local / G.nfg[p];
+    // the plan's half-length picks its compile-time body (one branch per CTA)
+    switch (A.L) {
+        case 64: fwd_body<T, 64, false>(A, fg, jh); break;
+        case 128: fwd_body<T, 128, false>(A, fg, jh); break;
+        case 256: fwd_body<T, 256, false>(A, fg, jh); break;
+        case 320: fwd_body<T, 320, false>(A, fg, jh); break;
+        case 512: fwd_body<T, 512, false>(A, fg, jh); break;
+        case 640: fwd_body<T, 640, false>(A, fg, jh); break;
+        case 1024: fwd_body<T, 1024, false>(A, fg, jh); break;
+        case 1280: fwd_body<T, 1280, false>(A, fg, jh); break;
+        default: fwd_body<T, -1, false>(A, fg, jh);
+    }
 }
 
 template <typename T>
@@ -949,7 +962,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     int p = 0;
     while (p + 1 < G.n && b >= G.cta_start[p + 1]) ++p;
     const int local = b - G.cta_start[p];
-    inv_body<T, 0>(G.a[p], local % G.nfg[p], local / G.nfg[p]);
+    const InvArgs<T>& A = G.a[p];
+    const int fg = local % G.nfg[p], jh = local / G.nfg[p];
+    switch (A.L) {
+        case 64: inv_body<T, 64>(A, fg, jh); break;
+        case 128: inv_body<T, 128>(A, fg, jh); break;
+        case 256: inv_body<T, 256>(A, fg, jh); break;
+        case 320: inv_body<T, 320>(A, fg, jh); break;
+        case 512: inv_body<T, 512>(A, fg, jh); break;
+        case 640: inv_body<T, 640>(A, fg, jh); break;
+        case 1024: inv_body<T, 1024>(A, fg, jh); break;
+        case 1280: inv_body<T, 1280>(A, fg, jh); break;
+        default: inv_body<T, -1>(A, fg, jh);
+    }
 }
 
 // ---- reduced grids: a half-length per latitude pair -------------------
