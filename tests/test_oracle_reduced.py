@@ -109,3 +109,22 @@ def test_synthesis_matches_full_grid_at_shared_longitudes():
         step = I // Ij[j]
         np.testing.assert_allclose(red[:, off[j]:off[j + 1]], full[:, j, ::step],
                                    rtol=0, atol=1e-14 * scale)
+
+
+def test_significant_wavenumbers_match_an_independent_legendre_routine():
+    # M_j from SciPy's associated Legendre functions (their own algorithm,
+    # normalised here by sqrt((2n+1)/2 (n-m)!/(n+m)!); the phase does not
+    # matter for a magnitude) equals the oracle's, at T31 where SciPy's
+    # factorials stay in range.
+    special = pytest.importorskip("scipy.special")
+    N, J, I = 31, 65, 128
+    mu = np.cos(np.arange(1, J + 1) * np.pi / (J + 1))
+    M = np.zeros(J, dtype=np.int64)
+    for m in range(N + 1):
+        for n in range(m, N + 1):
+            c = np.sqrt((2 * n + 1) / 2.0 *
+                        np.exp(special.gammaln(n - m + 1) - special.gammaln(n + m + 1)))
+            sig = np.abs(c * special.lpmv(m, n, mu)) >= 1e-16
+            M[sig] = np.maximum(M[sig], m)
+    _, Mo = O.reduced_sizes(N, J, I)
+    np.testing.assert_array_equal(Mo, M)
