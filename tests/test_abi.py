@@ -67,3 +67,41 @@ def test_null_and_foreign_handles(lib):
     bogus = ctypes.create_string_buffer(256)
     assert lib.sht_forward(ctypes.addressof(bogus), None, None, None) == -6
     assert lib.sht_plan_destroy(ctypes.addressof(bogus)) == -6
+
+
+def _lat(pts):
+    return (ctypes.c_int * len(pts))(*pts)
+
+
+@pytest.mark.parametrize("N,J,pts", [
+    (15, 7, None),                                  # NULL I_lat
+    (15, 8, [32] * 8),                              # J even
+    (15, 7, [16, 24, 32, 40, 32, 24, 18]),          # not symmetric
+    (15, 7, [16, 25, 32, 40, 32, 25, 16]),          # odd count
+    (15, 7, [14, 24, 32, 40, 32, 24, 14]),          # 14/2 = 7: not 2-3-5 smooth
+    (15, 7, [16, 24, 32, 16384, 32, 24, 16]),       # count above 8192
+    (15, 7, [16, 24, 30, 30, 30, 24, 16]),          # widest row does not exceed 2N
+])
+def test_invalid_reduced_grids_rejected_on_host(lib, N, J, pts):
+    h = ctypes.c_void_p()
+    lib.sht_plan_create_reduced.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_void_p)]
+    arg = None if pts is None else ctypes.cast(_lat(pts), ctypes.c_void_p)
+    assert lib.sht_plan_create_reduced(N, J, arg, 1, 0, ctypes.byref(h)) == -1
+    assert not h.value
+    lib.sht_last_error.restype = ctypes.c_char_p
+    assert lib.sht_last_error()
+
+
+def test_newer_entry_points_reject_null_handles(lib):
+    vp = ctypes.c_void_p
+    lib.sht_reduced_grid_sizes.argtypes = [vp, ctypes.c_int, vp]
+    lib.sht_plan_grid_points.argtypes = [vp, vp]
+    lib.sht_profile_read_kernels.argtypes = [vp, vp, vp, vp]
+    lib.sht_prolong_spectral_add.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    buf = ctypes.create_string_buffer(1024)
+    assert lib.sht_reduced_grid_sizes(None, 0, buf) == -6
+    assert lib.sht_plan_grid_points(None, buf) == -6
+    assert lib.sht_profile_read_kernels(None, buf, buf, buf) == -6
+    assert lib.sht_prolong_spectral_add(None, buf, 0, buf, None) == -6
