@@ -21,16 +21,21 @@
 // row-to-row distance off a single bank; each pass reads its twiddles from
 // a table contiguous in the butterfly index.  Global loads are
 // asynchronous element copies (cp.async) straight into the padded layout,
-// all in flight before the CTA waits once.  The
-// CTAs of all field groups of one latitude are adjacent in the launch
-// order, so their partial-sector writes of the same workspace rows meet in
-// L2.
+// all in flight before the CTA waits once, except where the FP32 two-pass
+// lengths (L = Q x 32, Q >= 8) let the forward's first pass read the grid
+// rows into registers and the inverse's last pass write them from
+// registers.  The CTAs of all field groups of one latitude are adjacent in
+// the launch order, so their partial-sector writes of the same workspace
+// rows meet in L2.
 //
 // The half-lengths of the standard grids (64 ... 1280) have kernels
 // specialised at compile time: radices, spans, twiddle offsets and the
 // digit reversal are constants, so the index arithmetic needs no integer
 // division by a runtime value.  Other lengths use the same code with the
-// shape read at run time.
+// shape read at run time (radices up to 8: the larger ones only occur in
+// the standard lengths).  Grouped launches branch per CTA to the body of
+// their plan's length, and a reduced grid launches the compile-time kernel
+// once per row length it contains, over a list of latitude pairs.
 #include <math.h>
 
 #include <mutex>
