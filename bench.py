@@ -38,7 +38,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", default="T639")
+    ap.add_argument("--workload", default="T639",
+                    help="T31, T159, T319, T639 (one JSON line in the bench contract), "
+                         "or ensemble / ladder (the grouped ensemble and the nested "
+                         "restriction ladder, timed with CUDA events)")
     ap.add_argument("--grid", default="cc", choices=["cc", "fejer1", "reduced"],
                     help="latitude grid: Clenshaw-Curtis, the reduced Clenshaw-Curtis "
                          "grid of the 1e-16 reduction rule (Sec. 6), or the shifted grid of "
@@ -556,10 +559,101 @@ def native_arm(args):
     return 0
 
 
+def batch_arm(args):
+    """The two batched configurations that are not the headline: the uneven
+    ensemble (16 members x {T63, T127, T255, T511} x 64 field-levels) as one
+    group per stage, eagerly and as a CUDA-graph replay, and the nested
+    restriction ladder (a T511 grid of 64 fields to T255 and T127 spectra).
+    Timed with CUDA events after warm-up; one JSON line."""
+    import torch
+    from paper_1711_11296_gb300 import sht, workloads as W
+    torch.cuda.set_device(0)
+    prec = "bf16x3" if args.precision == "auto" else args.precision
+    steps = min(args.steps, 5) if prec == "fp64" else args.steps
+
+    def timeit(fn, n, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    line = {"metric": None, "unit": None, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "dtype": "f64" if prec == "fp64" else "f32+" + prec,
+            "data": "synthetic"}
+    if args.workload == "ensemble":
+        members = W.ENSEMBLE
+        plans = [sht.Plan(w.N, w.J, w.I, w.F, prec) for w in members]
+        grp = sht.Group(plans)
+        specs = [torch.from_numpy(W.workload_spectrum(w)).to(device="cuda",
+                                                            dtype=plans[0].complex_dtype)
+                 for w in members]
+        grids = [p.empty_grid() for p in plans]
+        outs = [p.empty_spec() for p in plans]
+
+        def pair():
+            grp.inverse(specs, out=grids)
+            grp.forward(grids, out=outs)
+
+        ms = timeit(pair, steps, args.warmup)
+        nfl = sum(w.F for w in members)
+        line.update({"metric": "ensemble field-level transform pairs/s", "unit": UNIT,
+                     "value": nfl / (ms / 1e3), "ms_per_step": ms,
+                     "config": {"workload": "ensemble",
+                                "members": ["%s (N=%d, J=%d, I=%d, F=%d)"
+                                            % (w.name, w.N, w.J, w.I, w.F) for w in members],
+                                "field_levels": nfl, "path": prec, "grouped": True}})
+        if prec != "fp64":
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                pair()
+            torch.cuda.current_stream().wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                pair()
+            msg = timeit(graph.replay, steps, args.warmup)
+            line["graph"] = {"value": nfl / (msg / 1e3), "ms_per_step": msg}
+        for p in plans:
+            p.status()
+    else:
+        fine = W.LADDER[0]
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        gen = torch.Generator(device="cuda").manual_seed(171111296)
+        x = torch.randn(fine.F, fine.J, fine.I, device="cuda", dtype=dt, generator=gen)
+        res = {}
+        for k, coarse in ((1, W.LADDER[1]), (2, W.LADDER[2])):
+            p = sht.Plan(coarse.N, coarse.J, coarse.I, coarse.F, prec)
+            out = p.empty_spec()
+            ms = timeit(lambda: p.restrict_nested(x, k, out=out), steps, args.warmup)
+            res["k%d" % k] = {"to": coarse.name, "ms": ms,
+                              "field_levels_per_s": coarse.F / (ms / 1e3)}
+            p.status()
+        line.update({"metric": "nested restriction field-levels/s",
+                     "unit": "field-levels/s", "value": res["k1"]["field_levels_per_s"],
+                     "ms_per_step": res["k1"]["ms"], "results": res,
+                     "config": {"workload": "ladder", "fine": fine.name, "path": prec,
+                                "field_levels": fine.F}})
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.workload in ("ensemble", "ladder") and args.impl == "reference":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the oracle arm times the single-plan workloads only"}))
+        return 0
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload in ("ensemble", "ladder"):
+        return batch_arm(args)
     return native_arm(args)
 
 
