@@ -19,6 +19,10 @@ not reproducible here, so these stand in for them):
   N(0,1) (n+1)^-1 / sqrt(2 (2n+1)).
 * ``"uniform^-1/3"``: Re and Im uniform in [1, 2] times (n+1)^-1/3 (the
   amplitude law of the aliasing experiment, Sec. 4.2).
+* ``"flat"``: Re and Im independent N(0,1) at every degree (white noise:
+  every zonal wavenumber and parity carries a comparable share, so that a
+  per-(m, parity) error check weighs the high wavenumbers as much as the
+  low ones).
 """
 from dataclasses import dataclass
 
@@ -92,6 +96,8 @@ def random_spectrum(N, F, envelope="n^-1.5", seed=SEED_BASE, field0=0):
         amp = (n + 1.0) ** -1.0 / np.sqrt(2.0 * (2.0 * n + 1.0))
     elif envelope == "uniform^-1/3":
         amp = (n + 1.0) ** (-1.0 / 3.0)
+    elif envelope == "flat":
+        amp = np.ones_like(n)
     else:
         raise ValueError(envelope)
     out = np.empty((len(n), F), dtype=np.complex128)

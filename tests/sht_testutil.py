@@ -35,3 +35,72 @@ def assert_fp64_close(got, ref, rel_l2_tol=FP64_REL_L2, rel_max_tol=FP64_REL_MAX
 def to_cuda(a, dtype):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda").to(dtype)
+
+
+# ---------------------------------------------------------------------------
+# Per-(m, parity) errors.  One Legendre problem of the transform is one zonal
+# wavenumber m and one parity q of n - m (Appendix B): a whole-output
+# relative L2 hides a wrong or missing tile of a problem whose values are
+# small next to the output's norm, so the split-path tests also bound the
+# error of every problem relative to that problem's own values.
+# ---------------------------------------------------------------------------
+def spec_block_errors(got, ref, N, ms=None):
+    """Relative L2 error of every (m, parity) block of a packed spectrum.
+
+    got: [ncoef][F'] (columns already selected); ref: the same shape, or a
+    dict m -> [N-m+1][F'] (the oracle's selected zonal wavenumbers).  The
+    block (m, q) is the rows n = m + q, m + q + 2, ... of wavenumber m.
+    Returns {(m, q): error} over ``ms`` (default every m)."""
+    got = np.asarray(got)
+    ms = range(N + 1) if ms is None else ms
+    out = {}
+    for m in ms:
+        r0 = m * (N + 1) - m * (m - 1) // 2
+        g = got[r0:r0 + N - m + 1]
+        r = ref[m] if isinstance(ref, dict) else np.asarray(ref)[r0:r0 + N - m + 1]
+        for q in (0, 1):
+            gb, rb = g[q::2], r[q::2]
+            if rb.size == 0:
+                continue
+            out[(m, q)] = rel_l2(gb, rb)
+    return out
+
+
+def fold_rows(north, south):
+    """Zonal Fourier coefficients m of latitude rows (NumPy's real FFT with
+    1/I) folded into the parts of Appendix B: S = (X_north + X_south)/2
+    (n - m even) and A = (X_north - X_south)/2 (n - m odd).  north, south:
+    real [F][R][I], row r of ``south`` the mirror of row r of ``north``
+    (pass the Equator row as its own mirror).  Returns S, A [F][R][I/2+1]."""
+    I = north.shape[-1]
+    Xn = np.fft.rfft(north, axis=-1) / I
+    Xs = np.fft.rfft(south, axis=-1) / I
+    return (Xn + Xs) / 2, (Xn - Xs) / 2
+
+
+def grid_block_errors(got_n, got_s, ref_n, ref_s, N, floor=0.0):
+    """Relative L2 error of every (m, parity) block of a synthesised grid,
+    from mirror-row pairs (see ``fold_rows``): block (m, 0) is S^m over the
+    rows and fields, (m, 1) is A^m.  Blocks whose reference norm is below
+    ``floor`` times the largest block norm (A^m vanishes at the Equator, and
+    some blocks are empty for m = N) are skipped.  Returns {(m, q): error}."""
+    gS, gA = fold_rows(got_n, got_s)
+    rS, rA = fold_rows(ref_n, ref_s)
+    norms = {}
+    for m in range(N + 1):
+        norms[(m, 0)] = np.linalg.norm(rS[..., m])
+        norms[(m, 1)] = np.linalg.norm(rA[..., m])
+    top = max(norms.values())
+    out = {}
+    for m in range(N + 1):
+        for q, g, r in ((0, gS, rS), (1, gA, rA)):
+            if norms[(m, q)] <= floor * top or norms[(m, q)] == 0.0:
+                continue
+            out[(m, q)] = np.linalg.norm(g[..., m] - r[..., m]) / norms[(m, q)]
+    return out
+
+
+def worst(errs):
+    """(largest error, its (m, parity) key) of a block-error dict."""
+    k = max(errs, key=errs.get)
+    return errs[k], k

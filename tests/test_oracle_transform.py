@@ -167,3 +167,31 @@ def test_adjoint_dot_products_t31():
     lhs = np.sum(O.synthesis(a_im0, N, J, I) * x)
     rhs = np.sum(np.real(np.conj(a_im0) * O.adjoint_synthesis(x, N)))
     assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+def test_synthesis_rows_matches_scipy_at_scattered_latitudes():
+    # synthesis_rows (Eq. iSHT at chosen 1-based latitudes) pinned against
+    # SciPy's spherical harmonics evaluated at those latitudes only, and
+    # against the full synthesis's rows: rows 1, J_h (the Equator) and J,
+    # unsorted, with a repeat, so that an off-by-one in the 1-based index or
+    # a dropped row ordering fails.
+    N, J, I = 12, 25, 28
+    Jh = (J + 1) // 2
+    rows = np.array([J, 1, Jh, 4, 1, J - 3])
+    a = W.random_spectrum(N, 2, "n^-1.5", seed=21)
+    got = O.synthesis_rows(a, N, J, I, rows)
+    assert got.shape == (2, len(rows), I)
+    th = O.cc_nodes(J)[0][rows - 1]
+    lam = 2 * np.pi * np.arange(I) / I
+    T, L = np.meshgrid(th, lam, indexing="ij")
+    for f in range(2):
+        ref = np.zeros((len(rows), I))
+        r = 0
+        for m in range(N + 1):
+            for n in range(m, N + 1):
+                y = np.sqrt(2 * np.pi) * (-1) ** m * special.sph_harm_y(n, m, T, L)
+                ref += (a[r, f].real * y).real if m == 0 else 2 * (a[r, f] * y).real
+                r += 1
+        np.testing.assert_allclose(got[f], ref, atol=1e-13)
+    full = O.synthesis(a, N, J, I)
+    np.testing.assert_allclose(got, full[:, rows - 1, :], rtol=0, atol=1e-15)
