@@ -186,15 +186,22 @@ int sht_inject_nested(sht_plan_t coarse, const void* fine_grid, int k, void* coa
  * this call needs none: it computes the same result as sht_forward on an
  * FP64 plan of these sizes, rebuilding the nodes, weights, P~ table, FFT
  * tables and Fourier workspace in one fixed scratch array of
- * SHT_NOALLOC_SCRATCH_BYTES that the library keeps on every device that
- * loads it, for the life of the process.  It calls no allocator.
+ * SHT_NOALLOC_SCRATCH_BYTES.  It calls no allocator.
  *   grid: device double [nfields][J][I]; spec: device complex double
- *   [ncoef][nfields]; size rules as for sht_plan_create.  Sizes whose
- *   tables and workspace exceed the scratch array are rejected with
- *   SHT_ERR_ARG and a message giving the bytes needed (T127 with J = 257,
- *   I = 512 fits up to 46 fields).
- * The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ *   [ncoef][nfields]; size rules as for sht_plan_create (SHT_ERR_ARG for
+ *   invalid sizes, SHT_ERR_UNSUPPORTED for an I too long for the
+ *   shared-memory FFT).  Sizes whose tables and workspace exceed the
+ *   scratch array are rejected with SHT_ERR_ARG and a message giving the
+ *   bytes needed (T127 with J = 257, I = 512 fits up to 46 fields).
+ * The scratch array lives in the library's device module, which the CUDA
+ * runtime loads into a context on first use (lazily, by default): the first
+ * call on a device (per context) commits the 32 MiB, which then stays until
+ * the process exits.  Make that first call at start-up, before other code
+ * takes the device memory; if the array cannot be loaded the call returns
+ * SHT_ERR_CUDA with a message saying so.  A call that is not being captured
+ * looks the array's address up in the current context; a call under stream
+ * capture uses the address its context remembered from an earlier call, so
+ * make the first call before any capture (SHT_ERR_ARG otherwise).
  * Every call overwrites the array: calls that overlap on the GPU race, so
  * serialise them (one stream, or events).  Each call rewrites every entry
  * it reads, so results never depend on an earlier call. */
@@ -338,6 +345,17 @@ int sht_profile_enable(sht_plan_t plan, int on);
 int sht_profile_read(sht_plan_t plan, double* ms, long long* launches);
 int sht_profile_read_kernels(sht_plan_t plan, double* ms, long long* launches,
                              long long* kernels);
+
+/* Pipe throughput probe (instrumentation, no counterpart in the paper):
+ * the rate of one resident wave of CTAs per SM running chains of
+ * independent fused multiply-adds in registers, the ceiling against which
+ * the FP64 Legendre contraction (kind 0: DFMA) and the FP32 FFT arithmetic
+ * (kind 1: FFMA; kind 2: paired fma.rn.f32x2) are reported.  Calibrates its
+ * trip count to about 20 ms per launch, runs `reps` (1..100) launches on
+ * `stream` and writes the best rate in TFLOP/s (2 flops per FMA) to
+ * *tflops (host).  Synchronous; allocates nothing; SHT_ERR_ARG for a bad
+ * kind, reps or a NULL tflops, SHT_ERR_CUDA if a launch fails. */
+int sht_measure_fma_peak(int kind, int reps, void* stream, double* tflops);
 
 /* Message of the last error on this thread ("" if none). */
 const char* sht_last_error(void);

@@ -21,6 +21,9 @@ Contents (all FP64 except the binary128 Legendre recurrence of Sec. 4.1):
 * ``dft_forward``, ``dft_inverse`` -- Eq. (dFT) discretised, and its inverse
 * ``analysis``, ``synthesis``      -- Eq. (dSHT)/(cc-quad), Eq. (iSHT)/(iLT)
 * ``adjoint_analysis``, ``adjoint_synthesis`` -- transposes of the two
+  (``adjoint_analysis_rows`` and ``adjoint_synthesis(..., ms=...)``
+  evaluate them at chosen latitudes or zonal wavenumbers only)
+* ``synthesis_rows``               -- Eq. (iSHT) at chosen latitudes
 * ``restrict_nested``              -- Sec. 3.2 / Appendix C
 * ``reduced_sizes``, ``analysis_reduced``, ``synthesis_reduced`` -- reduced
                                       Clenshaw-Curtis grids with per-latitude

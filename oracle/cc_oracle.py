@@ -256,16 +256,24 @@ def _analysis_general(x, N, pfun, w, ms=None):
     return out
 
 
-def analysis(x, N, ms=None):
+def pnm_tables(N, J, ms):
+    """{m: pnm_cc(N, J, m, m)} for the zonal wavenumbers ``ms``: the P~
+    tables of ``analysis``, built once ahead of repeated transforms."""
+    return {m: pnm_cc(N, J, m, m) for m in ms}
+
+
+def analysis(x, N, ms=None, pnm=None):
     """Forward SHT on the Clenshaw-Curtis grid, Eq. (dSHT) with the zonal
     DFT and Eq. (cc-quad).  x: real [F][J][I] (j = 1 first).
 
     Returns the packed spectrum [ncoef][F] (complex), or, if ``ms`` is given,
-    a dict m -> [N-m+1][F] for those zonal wavenumbers only."""
+    a dict m -> [N-m+1][F] for those zonal wavenumbers only.  ``pnm``: the
+    P~ tables of ``pnm_tables`` (built here if None)."""
     x = np.asarray(x, dtype=np.float64)
     F, J, I = x.shape
     w = cc_weights(J)
-    d = _analysis_general(x, N, lambda m: pnm_cc(N, J, m, m), w, ms)
+    pf = (lambda m: pnm_cc(N, J, m, m)) if pnm is None else (lambda m: pnm[m])
+    d = _analysis_general(x, N, pf, w, ms)
     if ms is not None:
         return d
     spec = np.zeros((ncoef(N), F), dtype=np.complex128)
@@ -361,20 +369,44 @@ def adjoint_analysis(abar, N, J, I):
     return np.real(X @ E) * (w[None, :, None] / I)
 
 
-def adjoint_synthesis(xbar, N):
+def adjoint_analysis_rows(abar, N, J, I, rows):
+    """``adjoint_analysis`` evaluated only at the 1-based latitudes ``rows``
+    (all longitudes): the same formula with P~ and w taken at those nodes.
+    Returns real [F][len(rows)][I]."""
+    abar = np.asarray(abar, dtype=np.complex128)
+    F = abar.shape[1]
+    rows = np.asarray(rows)
+    w = cc_weights(J)[rows - 1]
+    X = np.zeros((F, len(rows), N + 1), dtype=np.complex128)
+    for m in range(N + 1):
+        a = abar[coef_offset(N, m):coef_offset(N, m) + N - m + 1]
+        X[:, :, m] = legendre_inverse_m(a, pnm_cc(N, J, m, m, j=rows))
+    E = _twiddle(I, np.arange(N + 1), +1.0).T           # [N+1][I]
+    return np.real(X @ E) * (w[None, :, None] / I)
+
+
+def adjoint_synthesis(xbar, N, ms=None):
     """Transpose of ``synthesis`` (grid -> spectrum).
 
     a~_n^m = c_m sum_j P~_n^m(mu_j) sum_i x~_ij e^{-i m lambda_i}, c_0 = 1,
-    c_m = 2 (m >= 1); the m = 0 imaginary part is zero."""
+    c_m = 2 (m >= 1); the m = 0 imaginary part is zero.  Returns the packed
+    spectrum [ncoef][F], or, if ``ms`` is given, a dict m -> [N-m+1][F] for
+    those zonal wavenumbers only."""
     xbar = np.asarray(xbar, dtype=np.float64)
     F, J, I = xbar.shape
-    X = dft_forward(xbar, N) * I                      # no 1/I
-    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
-    for m in range(N + 1):
+    ml = list(range(N + 1)) if ms is None else list(ms)
+    X = dft_forward(xbar, N, ms=ml) * I               # no 1/I
+    out = {}
+    for k, m in enumerate(ml):
         P = pnm_cc(N, J, m, m)
-        a = (2.0 if m >= 1 else 1.0) * (P @ X[:, :, m].T)
+        a = (2.0 if m >= 1 else 1.0) * (P @ X[:, :, k].T)
         if m == 0:
             a = a.real + 0j
+        out[m] = a
+    if ms is not None:
+        return out
+    spec = np.zeros((ncoef(N), F), dtype=np.complex128)
+    for m, a in out.items():
         spec[coef_offset(N, m):coef_offset(N, m) + N - m + 1] = a
     return spec
 
@@ -421,7 +453,8 @@ def orthonormality_errors(N, J, m, pnm=None, w=None):
     return eN, eO
 
 
-__all__ += ["orthonormality_errors", "cc_node_binary128", "synthesis_rows"]
+__all__ += ["orthonormality_errors", "cc_node_binary128", "synthesis_rows",
+            "adjoint_analysis_rows", "pnm_tables"]
 
 
 # --------------------------------------------------------------------------

@@ -89,6 +89,8 @@ int check_plan(const sht_plan_s* p) {
 
 }  // namespace
 
+void clear_error() { g_error.clear(); }
+
 void set_error(const char* fmt, ...) {
     char buf[512];
     va_list ap;

@@ -21,8 +21,9 @@ constexpr int kMaxGroup = 8;    // plans per grouped launch
 // stream capture, make no host API call).  Returns the CUDA status.
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
 
-// Thread-local error message set by the C entry points.
+// Thread-local error message set by the C entry points (cleared at entry).
 void set_error(const char* fmt, ...);
+void clear_error();
 
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };

@@ -10,14 +10,20 @@
 // call, with the same kernels the plan-based sht_forward uses.  The caller
 // passes only the grid and the spectrum.
 //
-// The array is SHT_NOALLOC_SCRATCH_BYTES long and every GPU that loads the
-// library holds it until the process exits.  Its device address is looked
-// up once per device, on the first call made with that device current.
-// Every call overwrites it, so calls that overlap on the GPU (on different
+// The array is SHT_NOALLOC_SCRATCH_BYTES long.  It belongs to this file's
+// device module, which the CUDA runtime loads into a context on first use
+// (lazily, by default): the first call on a device commits the 32 MiB, and
+// every later call in that context finds it there until the process exits.
+// A call that is not being captured looks the array's device address up in
+// the current context (with the device current) and remembers it per
+// context; a call under stream capture uses the remembered address, so the
+// first call in a context must come before any capture.  Every call
+// overwrites the array, so calls that overlap on the GPU (on different
 // streams, or from several threads) race; each call rewrites every entry it
 // later reads, so nothing depends on the previous call's contents.
-#include <mutex>
+#include <cuda.h>
 
+#include "sht_ctx_cache.h"
 #include "sht_internal.h"
 
 namespace sht {
@@ -29,24 +35,72 @@ cudaError_t launch_build_fwd_tiles(int N, int C, int4* tiles, cudaStream_t s);
 
 namespace {
 
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SHT_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {nullptr};
+ContextAddressCache<kMaxContexts> g_scratch_cache;
 
-// Device address of the scratch array on the current device `dev`.
-cudaError_t scratch_address(int dev, unsigned char** out) {
-    std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (!g_addr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = ptr;
-    }
-    *out = static_cast<unsigned char*>(g_addr[dev]);
+// The driver's cuCtxGetCurrent, reached through the runtime (no link
+// against libcuda): the key of the per-context address memo.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+cudaError_t current_context(const void** ctx) {
+    static CtxGetCurrent fn = nullptr;
+    static cudaError_t init = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e == cudaSuccess && q != cudaDriverEntryPointSuccess) e = cudaErrorNotSupported;
+        fn = reinterpret_cast<CtxGetCurrent>(f);
+        return e;
+    }();
+    if (init != cudaSuccess) return init;
+    CUcontext c = nullptr;
+    if (fn(&c) != CUDA_SUCCESS || !c) return cudaErrorDeviceUninitialized;
+    *ctx = c;
     return cudaSuccess;
+}
+
+// Device address of the scratch array in the current context; see the file
+// comment for when it is looked up and when the remembered one is used.
+int scratch_address(cudaStream_t s, unsigned char** out) {
+    const void* ctx = nullptr;
+    cudaError_t e = current_context(&ctx);
+    if (e != cudaSuccess) {
+        set_error("no current CUDA context: %s", cudaGetErrorString(e));
+        return SHT_ERR_CUDA;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) {
+        set_error("cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+        return SHT_ERR_CUDA;
+    }
+    cudaError_t lookup_err = cudaSuccess;
+    void* addr = nullptr;
+    const int rc = scratch_for_context(
+        g_scratch_cache, ctx, cs != cudaStreamCaptureStatusNone,
+        [&](void** a) {
+            lookup_err = cudaGetSymbolAddress(a, g_noalloc_scratch);
+            return lookup_err == cudaSuccess ? 0 : 1;
+        },
+        &addr);
+    if (rc == kScratchNeedsSetup) {
+        set_error("sht_forward_noalloc under stream capture before any uncaptured call "
+                  "in this context: make the first call before capturing");
+        return SHT_ERR_ARG;
+    }
+    if (rc != kScratchOk) {
+        set_error("the %u-byte scratch array is not available in this context (%s); it "
+                  "is committed when the first call loads it, so make that call at "
+                  "start-up, before other code takes the device memory",
+                  (unsigned)SHT_NOALLOC_SCRATCH_BYTES, cudaGetErrorString(lookup_err));
+        return SHT_ERR_CUDA;
+    }
+    *out = static_cast<unsigned char*>(addr);
+    return SHT_OK;
 }
 
 // Recurrence coefficients, the same formulas as plan creation (IEEE sqrt
@@ -97,6 +151,7 @@ using namespace sht;
 extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
                                    const double* grid, double* spec,
                                    void* stream) {
+    clear_error();
     if (N < 0 || J < 1 || J % 2 == 0 || I % 2 != 0 || I <= 2 * N || I > kMaxI ||
         nfields < 1) {
         set_error("invalid sizes N=%d J=%d I=%d nfields=%d", N, J, I, nfields);
@@ -128,7 +183,7 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     t.fft_smem = fft_smem_bytes(I, t.G, true);
     if (t.fft_smem > 227 * 1024) {
         set_error("I = %d too large for the shared-memory FFT", I);
-        return SHT_ERR_ARG;
+        return SHT_ERR_UNSUPPORTED;
     }
     const int C = 2 * nfields;
     t.ntiles_fwd = legendre_fwd_tile_count(N, C);
@@ -161,16 +216,10 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
         set_error("no CUDA device: %s", cudaGetErrorString(e));
         return SHT_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device %d out of range", dev);
-        return SHT_ERR_UNSUPPORTED;
-    }
+    cudaStream_t s = (cudaStream_t)stream;
     unsigned char* base = nullptr;
-    e = scratch_address(dev, &base);
-    if (e != cudaSuccess) {
-        set_error("cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        return SHT_ERR_CUDA;
-    }
+    const int arc = scratch_address(s, &base);
+    if (arc != SHT_OK) return arc;
     t.device = dev;
     t.d_mu = (double*)(base + o_mu);
     t.d_sin = (double*)(base + o_sn);
@@ -186,7 +235,6 @@ extern "C" int sht_forward_noalloc(int N, int J, int I, int nfields,
     t.d_tiles_fwd = (int4*)(base + o_til);
     t.d_work = base + o_wrk;
 
-    cudaStream_t s = (cudaStream_t)stream;
     const int th = 128;
     e = build_node_tables(&t, s);
     if (e == cudaSuccess) {

@@ -82,3 +82,37 @@ def test_roofline_of_the_fp64_and_split_contractions():
 def test_job_throughput_counts_all_ranks():
     # 2 ranks x 256 field-levels x 100 steps in 5600 ms
     assert bench.job_throughput(2, 256, 100, 5600.0) == pytest.approx(2 * 256 * 100 / 5.6)
+
+
+def test_step_bytes_is_both_ffts_and_both_contractions():
+    want = (2 * bench.fft_bytes(T639, 256, 4) + bench.split_gemm_bytes(T639, 256, "bf16x3", False)
+            + bench.split_gemm_bytes(T639, 256, "bf16x3", True))
+    assert bench.step_bytes(T639, 256, "bf16x3") == want
+    # the ensemble's grouped pair is the members' steps
+    assert bench.group_pair_bytes(W.ENSEMBLE, "bf16x3") == sum(
+        bench.step_bytes(w, w.F, "bf16x3") for w in W.ENSEMBLE)
+
+
+def test_fp64_roofline_uses_the_measured_pipe_peak():
+    pk = dict(PEAKS, fp64_tflops=1.3, dfma_probe=1.3, dgemm=1.1)
+    r = bench.roofline_for("legendre_forward", 12060.0, 100, T639, 256, "fp64", pk, "m")
+    assert r["peak"] == 1.3 and "measured" in r["peak_source"]
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.3)
+
+
+def test_both_arms_name_the_same_workload():
+    args = bench.parse_args([])
+    native = bench.workload_config(T639, 256, args, T639.J * T639.I, 4, 1)
+    ref = bench.workload_config(T639, 256, args, T639.J * T639.I, 4, args.gpus)
+    assert native == ref
+    assert native["workload"] == "T639" and native["field_levels_per_gpu"] == 256
+
+
+def test_oracle_sample_excludes_table_construction():
+    # the tables are built by oracle_tables, before and outside the timer;
+    # the sample then only transforms
+    w = W.WORKLOADS["T31"]
+    ms, tables = bench.oracle_tables(w, 4)
+    assert ms == list(range(0, 32, 4)) and sorted(tables) == ms
+    sec, frac = bench.oracle_sample(w, ms, tables)
+    assert sec > 0 and frac == pytest.approx(sum(32 - m for m in ms) / (32 * 33 // 2))

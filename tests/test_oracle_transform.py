@@ -195,3 +195,34 @@ def test_synthesis_rows_matches_scipy_at_scattered_latitudes():
         np.testing.assert_allclose(got[f], ref, atol=1e-13)
     full = O.synthesis(a, N, J, I)
     np.testing.assert_allclose(got, full[:, rows - 1, :], rtol=0, atol=1e-15)
+
+
+def test_sampled_adjoints_equal_the_dense_transposes_parts():
+    # adjoint_analysis_rows and adjoint_synthesis(ms=...) against the full
+    # adjoints, which the dense-transpose test above pins; scattered rows
+    # (1, the Equator, J, unsorted) and wavenumbers (0, the last, unsorted).
+    N, J, I = 4, 11, 10
+    A = _dense(lambda x: O.analysis(x, N), (1, J, I), False)
+    nc = O.ncoef(N)
+    a = W.random_spectrum(N, 2, "n^-1.5", seed=23)
+    rows = np.array([J, 1, (J + 1) // 2, 3])
+    got = O.adjoint_analysis_rows(a, N, J, I, rows)
+    full = O.adjoint_analysis(a, N, J, I)
+    np.testing.assert_allclose(got, full[:, rows - 1, :], rtol=0, atol=1e-15)
+    # and directly against the dense transpose of the analysis
+    v = np.concatenate([a[:, 0].real, a[:, 0].imag])
+    dense = (A.T @ v).reshape(J, I)
+    np.testing.assert_allclose(got[0], dense[rows - 1], rtol=0, atol=1e-14)
+    x = W.random_grid(2, J, I, seed=24)
+    ms = [N, 0, 2]
+    d = O.adjoint_synthesis(x, N, ms=ms)
+    full = O.adjoint_synthesis(x, N)
+    for m in ms:
+        r0 = O.coef_offset(N, m)
+        np.testing.assert_allclose(d[m], full[r0:r0 + N - m + 1], rtol=0, atol=1e-15)
+    S = _dense(lambda s: O.synthesis(s, N, J, I), (nc, 1), True)
+    t = S.T @ x[0].ravel()
+    dense = t[:nc] + 1j * t[nc:]
+    for m in ms:
+        r0 = O.coef_offset(N, m)
+        np.testing.assert_allclose(d[m][:, 0], dense[r0:r0 + N - m + 1], rtol=0, atol=1e-14)

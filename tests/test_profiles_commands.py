@@ -1,9 +1,10 @@
 """The commands quoted in profiles/ run committed files only: every
 `python bench.py ...` line there parses with bench.py's own arguments, and
-no command names a working-file folder."""
+every Python file a command names exists in the repository and is not
+ignored by git (so a reader can rerun it from a checkout)."""
 import os
-import re
 import shlex
+import subprocess
 import sys
 
 import bench
@@ -24,12 +25,23 @@ def _commands():
     return out
 
 
+def _ignored(path):
+    if not os.path.isdir(os.path.join(ROOT, ".git")):
+        return False
+    r = subprocess.run(["git", "-C", ROOT, "check-ignore", "-q", path],
+                       capture_output=True)
+    return r.returncode == 0
+
+
 def test_profile_commands_parse_with_bench_arguments(monkeypatch):
     cmds = _commands()
     assert cmds, "no bench command quoted in profiles/"
     for fn, line in cmds:
-        assert "_work" not in line and "gpurun_out/" not in line.split("bench.py")[1], (fn, line)
-        toks = shlex.split(line[line.index("bench.py"):])
-        args = [t for t in toks[1:] if not t.startswith("`")]
-        monkeypatch.setattr(sys, "argv", ["bench.py"] + args)
+        toks = shlex.split(line.replace("`", " "))
+        for t in toks:
+            if t.endswith(".py"):
+                assert os.path.exists(os.path.join(ROOT, t)), (fn, t)
+                assert not _ignored(t), (fn, t)
+        bt = shlex.split(line[line.index("bench.py"):].replace("`", " "))
+        monkeypatch.setattr(sys, "argv", ["bench.py"] + bt[1:])
         bench.parse_args()                      # SystemExit on an unknown flag
