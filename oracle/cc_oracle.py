@@ -554,3 +554,34 @@ def synthesis_reduced(spec, N, J, Ij):
     for j in range(J):
         out[:, off[j]:off[j + 1]] = dft_inverse(X[:, j, :K[j] + 1], int(Ij[j]))
     return out
+
+
+# --------------------------------------------------------------------------
+# Aliasing of quadratic and cubic terms (Sec. 4.2)
+# --------------------------------------------------------------------------
+def aliasing_products(specU, specV, specW, N, J, I, quad="cc"):
+    """Steps 2-3 of the aliasing experiment of Sec. 4.2: synthesise U, V, W
+    from their spectra (Eq. iSHT) on the J x I grid, form the quadratic and
+    cubic terms X_q = U V and X_c = U V W at every grid point, and analyse
+    both (Eq. dSHT with the zonal DFT and the grid's quadrature).
+
+    quad: "cc" (Clenshaw-Curtis nodes and weights, Eq. cc-quad) or "gauss"
+    (Gaussian nodes and weights, Eq. gauss-quad).  Spectra [ncoef][F];
+    returns (X_q, X_c) spectra [ncoef][F]."""
+    syn = synthesis if quad == "cc" else synthesis_gauss
+    ana = analysis if quad == "cc" else analysis_gauss
+    U = syn(specU, N, J, I)
+    V = syn(specV, N, J, I)
+    W = syn(specW, N, J, I)
+    Xq = U * V
+    Xc = Xq * W
+    return ana(Xq, N), ana(Xc, N)
+
+
+def aliasing_error(test, ref):
+    """Normalised aliasing error of Sec. 4.2 per stored (n, m):
+    |X_test - X_ref| / |X_ref| (elementwise over [ncoef][F])."""
+    return np.abs(np.asarray(test) - np.asarray(ref)) / np.abs(np.asarray(ref))
+
+
+__all__ += ["aliasing_products", "aliasing_error"]
