@@ -143,6 +143,23 @@ int sht_inverse(sht_plan_t plan, const void* spec, void* grid, void* stream);
 int sht_adjoint(sht_plan_t plan, int which, const void* in, void* out,
                 void* stream);
 
+/* Quadratic and cubic terms of the aliasing experiment (Sec. 4.2, steps 2
+ * and 3): synthesise U, V and W from their spectra (Eq. iSHT), form
+ * X_q = U V and X_c = U V W at every grid point, and analyse both
+ * (Eq. dSHT, Eq. dFT, Eq. cc-quad) into spec_q and spec_c.  The products are
+ * formed inside W's inverse FFT as it stores each point, so the grids are
+ * read and written once more than by a plain synthesis.
+ *   spec_u, spec_v, spec_w: device [ncoef][nfields] (read);
+ *   grid_q, grid_c: device [nfields][J][I], caller-owned work grids that
+ *     hold X_q and X_c on return;
+ *   spec_q, spec_c: device [ncoef][nfields] (written).
+ * Layouts and precision as sht_forward.  Five transforms on `stream`, one
+ * after another on the plan's workspace.  SHT_ERR_ARG for NULL or
+ * coinciding grids/spectra, SHT_ERR_UNSUPPORTED on reduced grids. */
+int sht_alias_products(sht_plan_t plan, const void* spec_u, const void* spec_v,
+                       const void* spec_w, void* grid_q, void* grid_c, void* spec_q,
+                       void* spec_c, void* stream);
+
 /* Restriction of a fine grid to the coarse plan's spectrum (Sec. 3.2 and
  * Appendix C): the coarse analysis of the sub-grid made of every 2^k-th
  * latitude starting from j = 2^k (1-based) and every 2^k-th longitude,

@@ -445,6 +445,40 @@ extern "C" int sht_adjoint(sht_plan_t p, int which, const void* in, void* out,
     return forward_scaled(p, in, plain_source(p), sc, out, s);
 }
 
+extern "C" int sht_alias_products(sht_plan_t p, const void* spec_u, const void* spec_v,
+                                  const void* spec_w, void* grid_q, void* grid_c,
+                                  void* spec_q, void* spec_c, void* stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!spec_u || !spec_v || !spec_w || !grid_q || !grid_c || !spec_q || !spec_c) {
+        set_error("NULL buffer");
+        return SHT_ERR_ARG;
+    }
+    if (grid_q == grid_c || spec_q == spec_c) {
+        set_error("the two grids and the two output spectra must be distinct buffers");
+        return SHT_ERR_ARG;
+    }
+    if (p->ragged) {
+        set_error("the products are built for full latitude rows only");
+        return SHT_ERR_UNSUPPORTED;
+    }
+    DeviceGuard dg(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // U into grid_q, V into grid_c, then W: its inverse FFT forms the
+    // products at each point as it stores (grid_q = U V, grid_c = U V W)
+    const InvScale plain{nullptr, 1.0};
+    rc = inverse_impl(p, spec_u, plain, grid_q, s);
+    if (rc) return rc;
+    rc = inverse_impl(p, spec_v, plain, grid_c, s);
+    if (rc) return rc;
+    InvScale prod{nullptr, 1.0, 2, grid_c};
+    rc = inverse_impl(p, spec_w, prod, grid_q, s);
+    if (rc) return rc;
+    rc = forward_impl(p, grid_q, plain_source(p), spec_q, s);
+    if (rc) return rc;
+    return forward_impl(p, grid_c, plain_source(p), spec_c, s);
+}
+
 extern "C" int sht_restrict_nested(sht_plan_t p, const void* fine_grid, int k,
                                    void* coarse_spec, void* stream) {
     int rc = check_plan(p);

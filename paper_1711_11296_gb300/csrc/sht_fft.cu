@@ -476,7 +476,11 @@ struct InvArgs {
     const long long* rowoff;   // reduced grid: first point of each row (null: regular)
     long long fstride;         // reduced grid: points per field
     const int* jh_list;        // latitude pair of each CTA row (null: blockIdx.y)
-    int accumulate;            // 1: grid += rows (prolongation of a correction)
+    int accumulate;            // 1: grid += rows (prolongation of a correction);
+                               // 2: products (Sec. 4.2): with w the synthesised
+                               // value, grid holds u and becomes u v, grid2
+                               // holds v and becomes u v w
+    T* grid2;                  // second grid of the products (else null)
     int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
@@ -849,16 +853,17 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
         constexpr int Q = FS.radix[0];   // index per butterfly
         passes_fixed<T, LT, 0, 1>(rows, nrows, LP, tws);
         const V sgn = K::make(rs, -rs);   // x = conj(z) rs
-        // compiled with and without accumulation into the grid
-        auto last_pass = [&](auto acc) {
-            constexpr bool ACC = decltype(acc)::value;
+        // compiled for the plain store, accumulation into the grid and the
+        // products of the aliasing experiment
+        auto last_pass = [&](auto mode) {
+            constexpr int MODE = decltype(mode)::value;
             for (int idx = tid; idx < nrows * Q; idx += NT) {
                 const int r = idx / Q, b = idx - r * Q;
                 const int f = f0 + (r < nf ? r : r - nf);
                 const int j = (r < nf) ? jh : (A.J - 1 - jh);
-                V* xv = reinterpret_cast<V*>(
-                            A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
-                                     : A.grid + ((long long)f * A.J + j) * A.I) + b;
+                const long long off = A.rowoff ? (long long)f * A.fstride + A.rowoff[j]
+                                               : ((long long)f * A.J + j) * A.I;
+                V* xv = reinterpret_cast<V*>(A.grid + off) + b;
                 const V* zb = rows + (size_t)r * LP + ph<T>(b * R);
                 V a[R];
 #pragma unroll
@@ -867,27 +872,49 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
 #pragma unroll
                 for (int k1 = 0; k1 < R; ++k1) {
                     const V y = mul_f32x2(a[Dft<T, R>::pos(k1)], sgn);
-                    if constexpr (ACC)
+                    if constexpr (MODE == 1) {
                         xv[k1 * Q] = K::add(xv[k1 * Q], y);
-                    else
+                    } else if constexpr (MODE == 2) {
+                        V* x2 = reinterpret_cast<V*>(A.grid2 + off) + b;
+                        const V uv = mul_f32x2(xv[k1 * Q], x2[k1 * Q]);
+                        xv[k1 * Q] = uv;
+                        x2[k1 * Q] = mul_f32x2(uv, y);
+                    } else {
                         xv[k1 * Q] = y;
+                    }
                 }
             }
         };
-        if (A.accumulate)
-            last_pass(std::true_type{});
+        if (A.accumulate == 1)
+            last_pass(std::integral_constant<int, 1>{});
+        else if (A.accumulate == 2)
+            last_pass(std::integral_constant<int, 2>{});
         else
-            last_pass(std::false_type{});
+            last_pass(std::integral_constant<int, 0>{});
         return;
     }
     run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
 
+    // store of one synthesised pair of values y at xv[k] (x2: the second
+    // grid of the products)
+    auto put = [&](V* xv, V* x2, int k, V y) {
+        if (A.accumulate == 1) {
+            xv[k] = K::add(xv[k], y);
+        } else if (A.accumulate == 2) {
+            const V uv = K::make(xv[k].x * x2[k].x, xv[k].y * x2[k].y);
+            xv[k] = uv;
+            x2[k] = K::make(uv.x * y.x, uv.y * y.y);
+        } else {
+            xv[k] = y;
+        }
+    };
     for (int r = 0; r < nrows; ++r) {
         const int f = f0 + (r < nf ? r : r - nf);
         const int j = (r < nf) ? jh : (A.J - 1 - jh);
-        V* xv = reinterpret_cast<V*>(
-            A.rowoff ? A.grid + (long long)f * A.fstride + A.rowoff[j]
-                     : A.grid + ((long long)f * A.J + j) * A.I);
+        const long long off = A.rowoff ? (long long)f * A.fstride + A.rowoff[j]
+                                       : ((long long)f * A.J + j) * A.I;
+        V* xv = reinterpret_cast<V*>(A.grid + off);
+        V* x2 = A.grid2 ? reinterpret_cast<V*>(A.grid2 + off) : nullptr;
         const V* z = rows + (size_t)r * LP;
         if constexpr (LT > 0) {
             // all of the thread's shared-memory reads of the row first
@@ -901,16 +928,12 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
 #pragma unroll
             for (int i = 0; i < NIT; ++i) {
                 const int k = tid + i * NT;
-                if (LT % NT == 0 || k < LT) {
-                    const V y = K::make(v[i].x * rs, -v[i].y * rs);
-                    xv[k] = A.accumulate ? K::add(xv[k], y) : y;
-                }
+                if (LT % NT == 0 || k < LT) put(xv, x2, k, K::make(v[i].x * rs, -v[i].y * rs));
             }
         } else {
             for (int k = tid; k < L; k += NT) {
                 const V v = z[ph<T>(rev_of<T, LT>(k, A.rev))];
-                const V y = K::make(v.x * rs, -v.y * rs);
-                xv[k] = A.accumulate ? K::add(xv[k], y) : y;
+                put(xv, x2, k, K::make(v.x * rs, -v.y * rs));
             }
         }
     }
@@ -1128,6 +1151,7 @@ InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& 
     A.fstride = (long long)p->J * p->I;
     A.jh_list = nullptr;
     A.accumulate = sc.accumulate;
+    A.grid2 = static_cast<T*>(sc.grid2);
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);

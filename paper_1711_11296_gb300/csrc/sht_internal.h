@@ -71,7 +71,10 @@ struct FwdScale {
 struct InvScale {
     const double* rowscale;   // [Jh] per northern row (w_j/I or 1), may be null
     double mfactor1;          // factor for m >= 1 before the Hermitian sum
-    int accumulate = 0;       // 1: add the rows to the grid instead of writing them
+    int accumulate = 0;       // 1: add the rows to the grid instead of writing them;
+                              // 2: products of Sec. 4.2 (see grid2)
+    void* grid2 = nullptr;    // accumulate = 2: the grid holds u and becomes u v,
+                              // grid2 holds v and becomes u v w (w = the rows)
 };
 
 struct SplitTables;   // tensor-core operand tables (split plans)

@@ -124,6 +124,26 @@ class Plan:
                               _stream_ptr(self.device)))
         return out
 
+    def alias_products(self, spec_u, spec_v, spec_w, grids=None, out=None):
+        """Quadratic and cubic terms of the aliasing experiment (Sec. 4.2):
+        the analyses of U V and U V W, with U, V, W synthesised from their
+        spectra on this plan's grid.  ``grids``: two work grids (returned
+        holding U V and U V W); ``out``: two spectra.  Returns (spec_q,
+        spec_c)."""
+        for t, nm in ((spec_u, "spec_u"), (spec_v, "spec_v"), (spec_w, "spec_w")):
+            self._check(t, (self.ncoef, self.F), self.complex_dtype, nm)
+        grids = [self.empty_grid(), self.empty_grid()] if grids is None else grids
+        out = [self.empty_spec(), self.empty_spec()] if out is None else out
+        for g in grids:
+            self._check(g, self.grid_shape, self.real_dtype, "grid")
+        for o in out:
+            self._check(o, (self.ncoef, self.F), self.complex_dtype, "spec")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        check(lib.sht_alias_products(self._h, ptr(spec_u), ptr(spec_v), ptr(spec_w),
+                                     ptr(grids[0]), ptr(grids[1]), ptr(out[0]),
+                                     ptr(out[1]), _stream_ptr(self.device)))
+        return out[0], out[1]
+
     def restrict_nested(self, fine_grid, k, out=None):
         """Coarse spectrum of a fine grid with J_f = 2^k (J+1) - 1, I_f = 2^k I."""
         Jf, If = 2 ** k * (self.J + 1) - 1, 2 ** k * self.I

@@ -55,6 +55,12 @@ WORKLOADS = {
                      "4 fields x 64 levels"),
 }
 
+# The aliasing experiment of Sec. 4.2 at the paper's cubic Clenshaw-Curtis
+# resolution Tc479 (N = 479, J = 959; I = 4 (N + 1)), with the amplitude law
+# of its step 1; F field-levels per field U, V, W.
+ALIAS = Workload("Tc479", 479, 959, 1920, 64, "uniform^-1/3", 5,
+                 "quadratic and cubic terms of Sec. 4.2")
+
 # Uneven ensemble: 16 members x 32 levels x 2 fields at each truncation.
 ENSEMBLE = [
     Workload("ens-T63", 63, 129, 256, 1024, "energy^-2", 3),

@@ -81,22 +81,30 @@ def fold_rows(north, south):
 def grid_block_errors(got_n, got_s, ref_n, ref_s, N, floor=0.0):
     """Relative L2 error of every (m, parity) block of a synthesised grid,
     from mirror-row pairs (see ``fold_rows``): block (m, 0) is S^m over the
-    rows and fields, (m, 1) is A^m.  Blocks whose reference norm is below
-    ``floor`` times the largest block norm (A^m vanishes at the Equator, and
-    some blocks are empty for m = N) are skipped.  Returns {(m, q): error}."""
+    rows and fields, (m, 1) is A^m.  Empty blocks (A^m vanishes at the
+    Equator; some blocks are empty for m = N) are skipped.
+
+    Each error is relative to max(the block's own norm, ``floor`` times the
+    median block norm).  The zonal FFT of a row rounds every coefficient by
+    about the same amount (a share of the whole row's magnitude), so a block
+    whose values at the sampled rows are far below the typical block's (high
+    m away from the Equator) carries that rounding floor rather than its
+    contraction's error; ``floor`` measures such blocks against the floor.
+    Returns {(m, q): error}."""
     gS, gA = fold_rows(got_n, got_s)
     rS, rA = fold_rows(ref_n, ref_s)
     norms = {}
     for m in range(N + 1):
         norms[(m, 0)] = np.linalg.norm(rS[..., m])
         norms[(m, 1)] = np.linalg.norm(rA[..., m])
-    top = max(norms.values())
+    med = float(np.median([v for v in norms.values() if v > 0.0]))
     out = {}
     for m in range(N + 1):
         for q, g, r in ((0, gS, rS), (1, gA, rA)):
-            if norms[(m, q)] <= floor * top or norms[(m, q)] == 0.0:
+            if norms[(m, q)] == 0.0:
                 continue
-            out[(m, q)] = np.linalg.norm(g[..., m] - r[..., m]) / norms[(m, q)]
+            den = max(norms[(m, q)], floor * med)
+            out[(m, q)] = np.linalg.norm(g[..., m] - r[..., m]) / den
     return out
 
 

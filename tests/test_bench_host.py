@@ -116,3 +116,15 @@ def test_oracle_sample_excludes_table_construction():
     assert ms == list(range(0, 32, 4)) and sorted(tables) == ms
     sec, frac = bench.oracle_sample(w, ms, tables)
     assert sec > 0 and frac == pytest.approx(sum(32 - m for m in ms) / (32 * 33 // 2))
+
+
+def test_alias_step_bytes_by_hand():
+    # three syntheses and two analyses of F fields, plus the U and V grids
+    # read and the two product grids written inside W's inverse FFT (in
+    # place of W's grid: three grid passes more than the five transforms)
+    w = W.ALIAS
+    F = 64
+    grid = F * w.J * w.I * 4
+    inv = bench.fft_bytes(w, F, 4) + bench.split_gemm_bytes(w, F, "bf16x3", True)
+    fwd = bench.fft_bytes(w, F, 4) + bench.split_gemm_bytes(w, F, "bf16x3", False)
+    assert bench.alias_step_bytes(w, F, "bf16x3") == 3 * inv + 2 * fwd + 3 * grid
