@@ -512,14 +512,59 @@ def reduced_kmax(N, Ij):
     return np.minimum(N, np.asarray(Ij, dtype=np.int64) // 2 - 1)
 
 
-def analysis_reduced(x, N, J, Ij):
+def _row_phase(I, shift, ms, sign):
+    """exp(sign * 2 pi i * m * shift / I): the zonal phase of a row whose
+    longitudes are lambda_i = 2 pi (i + shift) / I.  ``shift`` is 0 or 1/2,
+    so the angle is reduced exactly as the integer (2 m shift) mod (2 I)."""
+    ms = np.asarray(ms, dtype=np.int64)
+    r = (ms * int(round(2 * shift))) % (2 * I)
+    ang = np.pi * r / I
+    return np.cos(ang) + sign * 1j * np.sin(ang)
+
+
+def octahedral_sizes(J, first=20, step=4):
+    """Longitude counts of the octahedral Clenshaw-Curtis grid (Sec. 6): the
+    j-th latitude from either pole (j = 1..J_h) carries first + step (j - 1)
+    points (ECMWF's octahedral pattern, 20 at the first row and 4 more per
+    row), mirrored about the Equator.  Returns I_j [J], j = 1 first."""
+    Jh = (J + 1) // 2
+    north = [first + step * (j - 1) for j in range(1, Jh + 1)]
+    return np.array(north + north[:J - Jh][::-1], dtype=np.int64)
+
+
+def icositetrahedral_sizes(J):
+    """Longitude counts and zonal shifts of the icositetrahedral
+    Clenshaw-Curtis grid (Sec. 6): 24 equal-area triangular panels, 6 around
+    each pole from the pole to 30 degrees of latitude and 12 in the tropical
+    belt.  The j-th latitude from either pole carries 6 j points (6 panels of
+    j points each) up to the row j30 nearest 30 degrees (theta = pi/3, so
+    j30 = round((J+1)/3)), and 6 j30 points on every tropical row; tropical
+    rows alternate between unshifted longitudes and longitudes shifted by
+    half a spacing (the phase shift in the zonal transform that the paper
+    names), counting from j30, which is unshifted.  Returns (I_j [J],
+    shift_j [J] in units of the row's spacing), j = 1 first."""
+    Jh = (J + 1) // 2
+    j30 = int(round((J + 1) / 3.0))
+    Ij = np.zeros(J, dtype=np.int64)
+    sh = np.zeros(J)
+    for j in range(1, Jh + 1):
+        Ij[j - 1] = 6 * min(j, j30)
+        sh[j - 1] = 0.5 * ((j - j30) % 2) if j > j30 else 0.0
+        Ij[J - j] = Ij[j - 1]
+        sh[J - j] = sh[j - 1]
+    return Ij, sh
+
+
+def analysis_reduced(x, N, J, Ij, shifts=None):
     """Forward SHT on a reduced Clenshaw-Curtis grid.
 
     x: real [F][sum I_j], latitude rows packed one after another (j = 1
     first).  Row j gives X^m(phi_j) by the zonal DFT of its I_j points
     (discretised Eq. dFT with 1/I_j) for m <= min(N, I_j/2 - 1), and 0 above;
-    then the quadrature of Eq. (cc-quad) over all J nodes.  Returns the
-    packed spectrum [ncoef][F]."""
+    then the quadrature of Eq. (cc-quad) over all J nodes.  ``shifts``
+    (default 0): row j's longitudes are lambda_i = 2 pi (i + shifts[j]) /
+    I_j, so its DFT carries the phase exp(-i m 2 pi shifts[j] / I_j).
+    Returns the packed spectrum [ncoef][F]."""
     x = np.asarray(x, dtype=np.float64)
     F = x.shape[0]
     off = reduced_row_offsets(Ij)
@@ -528,6 +573,9 @@ def analysis_reduced(x, N, J, Ij):
     for j in range(J):
         row = x[:, off[j]:off[j + 1]]
         X[:, j, :K[j] + 1] = dft_forward(row, int(K[j]))
+        if shifts is not None and shifts[j] != 0:
+            X[:, j, :K[j] + 1] *= _row_phase(int(Ij[j]), shifts[j],
+                                             np.arange(K[j] + 1), -1.0)
     w = cc_weights(J)
     spec = np.zeros((ncoef(N), F), dtype=np.complex128)
     for m in range(N + 1):
@@ -538,10 +586,11 @@ def analysis_reduced(x, N, J, Ij):
     return spec
 
 
-def synthesis_reduced(spec, N, J, Ij):
+def synthesis_reduced(spec, N, J, Ij, shifts=None):
     """Inverse SHT (Eq. iSHT via Eq. iLT) on a reduced Clenshaw-Curtis grid:
     X^m(phi_j) for every node, then row j is the inverse zonal DFT of
-    m <= min(N, I_j/2 - 1) on its I_j longitudes.  Returns [F][sum I_j]."""
+    m <= min(N, I_j/2 - 1) on its I_j longitudes (shifted by shifts[j]
+    spacings, as in ``analysis_reduced``).  Returns [F][sum I_j]."""
     spec = np.asarray(spec, dtype=np.complex128)
     F = spec.shape[1]
     X = np.zeros((F, J, N + 1), dtype=np.complex128)
@@ -552,7 +601,10 @@ def synthesis_reduced(spec, N, J, Ij):
     K = reduced_kmax(N, Ij)
     out = np.zeros((F, int(off[-1])), dtype=np.float64)
     for j in range(J):
-        out[:, off[j]:off[j + 1]] = dft_inverse(X[:, j, :K[j] + 1], int(Ij[j]))
+        Xj = X[:, j, :K[j] + 1]
+        if shifts is not None and shifts[j] != 0:
+            Xj = Xj * _row_phase(int(Ij[j]), shifts[j], np.arange(K[j] + 1), +1.0)
+        out[:, off[j]:off[j + 1]] = dft_inverse(Xj, int(Ij[j]))
     return out
 
 
@@ -584,4 +636,5 @@ def aliasing_error(test, ref):
     return np.abs(np.asarray(test) - np.asarray(ref)) / np.abs(np.asarray(ref))
 
 
-__all__ += ["aliasing_products", "aliasing_error"]
+__all__ += ["aliasing_products", "aliasing_error", "octahedral_sizes",
+            "icositetrahedral_sizes"]

@@ -7,6 +7,7 @@ failure on a grid that drops significant wavenumbers, and agreement with the
 full-grid synthesis at the longitudes the two grids share."""
 import numpy as np
 import pytest
+from scipy import special
 
 import oracle as O
 from oracle import cc_oracle as OC
@@ -128,3 +129,68 @@ def test_significant_wavenumbers_match_an_independent_legendre_routine():
             M[sig] = np.maximum(M[sig], m)
     _, Mo = O.reduced_sizes(N, J, I)
     np.testing.assert_array_equal(Mo, M)
+
+
+def test_octahedral_counts():
+    # 20 points on the first latitude from either pole, 4 more per row,
+    # mirrored about the Equator (J = 9: five rows from the north to it)
+    assert O.octahedral_sizes(9).tolist() == [20, 24, 28, 32, 36, 32, 28, 24, 20]
+    Ij = O.octahedral_sizes(1281)
+    assert Ij[640] == 20 + 4 * 640 and np.array_equal(Ij, Ij[::-1])
+
+
+def test_icositetrahedral_counts_and_shifts():
+    # the paper's Tc23 figure: J + 1 = 48 latitudes of 3.75 degrees, 30 N at
+    # row 16: 6 j points up to row 16, 96 on every tropical row, tropical
+    # rows alternately shifted by half a spacing from row 16 (unshifted)
+    Ij, sh = O.icositetrahedral_sizes(47)
+    assert Ij[:16].tolist() == [6 * j for j in range(1, 17)]
+    assert np.all(Ij[15:32] == 96)
+    assert np.array_equal(Ij, Ij[::-1]) and np.array_equal(sh, sh[::-1])
+    assert np.all(sh[:16] == 0.0)
+    assert sh[16:24].tolist() == [0.5, 0.0, 0.5, 0.0, 0.5, 0.0, 0.5, 0.0]
+    # 6 j30 points on the tropical rows: twice the J + 1 latitude spacings,
+    # the count of the cubic regular grid, I = 2 (J + 1)
+    assert Ij[23] == 2 * 48
+
+
+def test_shifted_rows_match_scipy_harmonics():
+    # synthesis on the icositetrahedral grid (shifted tropical rows) against
+    # SciPy's spherical harmonics evaluated at each row's own longitudes, row
+    # j summing the wavenumbers it carries, m <= min(N, I_j/2 - 1)
+    J, N = 23, 5
+    Ij, sh = O.icositetrahedral_sizes(J)
+    a = W.random_spectrum(N, 1, "n^-1.5", seed=61)[:, 0]
+    th = O.cc_nodes(J)[0]
+    ref = []
+    for j in range(J):
+        lam = 2 * np.pi * (np.arange(Ij[j]) + sh[j]) / Ij[j]
+        row = np.zeros(Ij[j])
+        r = 0
+        for m in range(N + 1):
+            for n in range(m, N + 1):
+                if m <= min(N, Ij[j] // 2 - 1):
+                    y = np.sqrt(2 * np.pi) * (-1) ** m * special.sph_harm_y(n, m, th[j], lam)
+                    row += (a[r].real * y).real if m == 0 else 2 * (a[r] * y).real
+                r += 1
+        ref.append(row)
+    got = O.synthesis_reduced(a[:, None], N, J, Ij, shifts=sh)[0]
+    np.testing.assert_allclose(got, np.concatenate(ref), atol=1e-13)
+    # and the shift matters: without it the tropical rows differ
+    plain = O.synthesis_reduced(a[:, None], N, J, Ij)[0]
+    assert np.abs(plain - got).max() > 1e-3
+
+
+def test_shifted_grid_round_trip_is_exact():
+    # every row of the Tc23 icositetrahedral grid carries m <= 2 (6 points
+    # at the first row) and J >= 2N+1: the transform pair is exact
+    J, N = 47, 2
+    Ij, sh = O.icositetrahedral_sizes(J)
+    a = W.random_spectrum(N, 3, "n^-1.5", seed=62)
+    g = O.synthesis_reduced(a, N, J, Ij, shifts=sh)
+    np.testing.assert_allclose(O.analysis_reduced(g, N, J, Ij, shifts=sh), a, atol=1e-14)
+    # the octahedral grid likewise for N = 9 (20 points at the first row)
+    Io = O.octahedral_sizes(J)
+    a = W.random_spectrum(9, 2, "n^-1.5", seed=63)
+    g = O.synthesis_reduced(a, 9, J, Io)
+    np.testing.assert_allclose(O.analysis_reduced(g, 9, J, Io), a, atol=1e-14)
