@@ -43,10 +43,12 @@ def parse_args(argv=None):
                          "or ensemble / ladder / alias (the grouped ensemble, the nested "
                          "restriction ladder and the aliasing products of Sec. 4.2, "
                          "timed with CUDA events)")
-    ap.add_argument("--grid", default="cc", choices=["cc", "fejer1", "reduced"],
+    ap.add_argument("--grid", default="cc",
+                    choices=["cc", "fejer1", "reduced", "octahedral", "icositetrahedral"],
                     help="latitude grid: Clenshaw-Curtis, the reduced Clenshaw-Curtis "
-                         "grid of the 1e-16 reduction rule (Sec. 6), or the shifted grid of "
-                         "Fejer's first rule")
+                         "grid of the 1e-16 reduction rule (Sec. 6), the octahedral or "
+                         "icositetrahedral Clenshaw-Curtis grid (Sec. 6), or the shifted "
+                         "grid of Fejer's first rule")
     ap.add_argument("--reduced-rule", default="fast", choices=["fast", "smooth"],
                     help="longitude counts of --grid reduced: lengths with compile-time "
                          "FFT kernels (fast) or any 2-3-5-smooth count (smooth)")
@@ -310,6 +312,10 @@ def workload_config(w, F, args, npts, real_bytes, world):
             "field_levels_per_gpu": F, "grid": args.grid,
             "grid_points_per_field": npts,
             "reduced_rule": args.reduced_rule if args.grid == "reduced" else None,
+            "longitudes": ("16 + 4 j on the j-th latitude from either pole"
+                           if args.grid == "octahedral" else
+                           "6 min(j, j30), tropical rows alternately shifted by half a "
+                           "spacing" if args.grid == "icositetrahedral" else None),
             "reduced_transform": bool(args.reduced),
             "step": "adjoint pair" if args.adjoint else "transform pair",
             "parallelism": "replicas" if world > 1 else "single",
@@ -436,7 +442,7 @@ def roofline_for(name, tot_ms, n, w, F, prec, pk, pk_src, npts=None, grid="cc"):
     if roof["peak"]:
         roof["frac"] = roof["achieved"] / roof["peak"]
     roof["ms_per_launch"] = 1000 * per_launch_s
-    t = MEASURED_TRAFFIC.get((name, prec, w.name, F)) if grid != "reduced" else None
+    t = MEASURED_TRAFFIC.get((name, prec, w.name, F)) if grid in ("cc", "fejer1") else None
     if t is not None:
         roof["traffic"] = t
         roof["traffic_note"] = ("ncu DRAM bytes of the T639 x 64 capture scaled by the "
@@ -468,6 +474,11 @@ def run_path(args, w, F, prec, device, dist, local, rank, world, e2e_wanted,
                          device=device).reduced_grid_sizes(args.reduced_rule)
         plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid="reduced",
                         lat_points=sizes)
+    elif args.grid in ("octahedral", "icositetrahedral"):
+        sizes, shift = ((sht.octahedral_grid_sizes(w.J), None) if args.grid == "octahedral"
+                        else sht.icositetrahedral_grid_sizes(w.J))
+        plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid="reduced",
+                        lat_points=sizes, half_shift=shift)
     else:
         plan = sht.Plan(w.N, w.J, w.I, F, prec, device=device, grid=args.grid)
     if args.reduced:
@@ -637,9 +648,9 @@ def transform_errors(w, prec, a, device, args, nf):
     split path's own grid."""
     import torch
     from paper_1711_11296_gb300 import sht
-    kw = dict(device=device, grid=args.grid) if args.grid != "reduced" else None
-    if kw is None:
+    if args.grid not in ("cc", "fejer1"):
         return None
+    kw = dict(device=device, grid=args.grid)
     p32 = sht.Plan(w.N, w.J, w.I, nf, prec, **kw)
     p64 = sht.Plan(w.N, w.J, w.I, nf, "fp64", **kw)
     a64 = torch.from_numpy(np.ascontiguousarray(a[:, :nf])).to(device)

@@ -314,8 +314,10 @@ int sht_plan_set_reduced(sht_plan_t plan, int on);
  *
  * sht_plan_create_reduced creates a plan on the Clenshaw-Curtis latitudes
  * of J nodes with I_lat[j] longitudes on latitude j (host array of J ints,
- * copied; each even, <= 8192, with I_lat[j]/2 a product of 2, 3 and 5, and
- * symmetric about the Equator; the largest must exceed 2N).  Grids of the
+ * copied; each even and <= 8192, symmetric about the Equator; the largest
+ * must exceed 2N).  Rows whose half-length has a prime factor above 5 are
+ * transformed by Bluestein's chirp-z method (two FFTs of a 2-3-5-smooth
+ * length >= I_lat[j] - 1), so every even count works, at a higher cost.  Grids of the
  * plan are device arrays [nfields][P] of P = sum_j I_lat[j] points, row j
  * (all its longitudes) after row j-1.  Row j carries the zonal wavenumbers
  * m <= min(N, I_lat[j]/2 - 1): the forward transform takes X^m(phi_j) from
@@ -336,6 +338,36 @@ int sht_reduced_grid_sizes(sht_plan_t plan, int rule, int* I_lat);
 int sht_plan_create_reduced(int N, int J, const int* I_lat, int nfields, int precision,
                             sht_plan_t* out);
 int sht_plan_grid_points(sht_plan_t plan, long long* npts);
+
+/* sht_plan_create_reduced with a zonal shift per latitude: half_shift[j] =
+ * 1 puts latitude j's longitudes half a spacing east of the meridian,
+ * lambda_i = 2 pi (i + 1/2) / I_lat[j], as on the tropical rows of the
+ * icositetrahedral grid (Sec. 6 names the phase shift this needs in the
+ * zonal transforms); 0 keeps lambda_i = 2 pi i / I_lat[j].  half_shift:
+ * host array of J ints, each 0 or 1, symmetric about the Equator.  The
+ * forward transform multiplies row j's X^m by e^{-i m pi / I_lat[j]}, the
+ * inverse by its conjugate.  Errors as sht_plan_create_reduced. */
+int sht_plan_create_reduced_shifted(int N, int J, const int* I_lat, const int* half_shift,
+                                    int nfields, int precision, sht_plan_t* out);
+
+/* Octahedral Clenshaw-Curtis grid (Sec. 6 proposes it; the counts are
+ * ECMWF's octahedral pattern): the j-th latitude from either pole (j = 1 ..
+ * (J+1)/2) carries first + step (j - 1) longitudes, mirrored about the
+ * Equator (first = 20, step = 4 is the usual octahedral grid).  Writes
+ * I_lat (host, J ints).  SHT_ERR_ARG for J even or < 1, first odd or < 2,
+ * step odd or < 0, or an Equator row above 8192.  Host only. */
+int sht_octahedral_grid_sizes(int J, int first, int step, int* I_lat);
+
+/* Icositetrahedral Clenshaw-Curtis grid (Sec. 6): 24 equal-area triangular
+ * panels, 6 around each pole down to 30 degrees of latitude and 12 in the
+ * tropical belt.  The j-th latitude from either pole carries 6 j
+ * longitudes (6 panels of j points) up to the latitude j30 = round((J+1)/3)
+ * nearest 30 degrees (theta = pi/3), and 6 j30 on every tropical row; the
+ * tropical rows after j30 alternate half_shift = 1, 0, 1, ... (a triangular
+ * lattice).  Writes I_lat and half_shift (host, J ints each) for
+ * sht_plan_create_reduced_shifted.  SHT_ERR_ARG for J even or < 1 or NULL
+ * arrays.  Host only. */
+int sht_icositetrahedral_grid_sizes(int J, int* I_lat, int* half_shift);
 
 /* Copy plan tables to host memory (test and inspection aid).  Any pointer
  * may be NULL.  w: J doubles (Eq. cc-wgt, all nodes); mu: J doubles

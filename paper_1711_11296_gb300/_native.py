@@ -21,7 +21,8 @@ EXPORTED = [
     "sht_plan_create_grid", "sht_plan_set_reduced", "sht_prolong_spectral",
     "sht_inject_nested", "sht_reduced_grid_sizes", "sht_plan_create_reduced",
     "sht_plan_grid_points", "sht_profile_read_kernels", "sht_prolong_spectral_add",
-    "sht_measure_fma_peak", "sht_alias_products",
+    "sht_measure_fma_peak", "sht_alias_products", "sht_plan_create_reduced_shifted",
+    "sht_octahedral_grid_sizes", "sht_icositetrahedral_grid_sizes",
 ]
 PROFILE_STAGES = 8
 STAGE_NAMES = ["fft_forward", "legendre_forward", "legendre_inverse",
@@ -86,6 +87,9 @@ def _load():
     lib.sht_plan_grid_points.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.sht_measure_fma_peak.argtypes = [i, i, vp, dp]
     lib.sht_alias_products.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.sht_plan_create_reduced_shifted.argtypes = [i, i, ip, ip, i, i, ctypes.POINTER(vp)]
+    lib.sht_octahedral_grid_sizes.argtypes = [i, i, i, ip]
+    lib.sht_icositetrahedral_grid_sizes.argtypes = [i, ip, ip]
     lib.sht_last_error.restype = ctypes.c_char_p
     lib.sht_version.restype = ctypes.c_char_p
     for name in EXPORTED:

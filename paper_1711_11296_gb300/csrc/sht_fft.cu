@@ -459,6 +459,9 @@ struct FwdArgs {
     unsigned* colmax;   // FP16 split plans: max |output| per real column (float bits)
     const long long* rowoff;   // reduced grid: first point of each row (null: regular)
     const int* jh_list;        // latitude pair of each CTA row (null: blockIdx.y)
+    const V* shiftph;          // rows shifted by half a spacing: e^{-i pi m / I_j} (else null)
+    const V* chirp;            // Bluestein rows: e^{-i pi n^2 / L}
+    const V* dft;              // Bluestein rows: DFT of the conjugate chirp / L2
     int F, J, Jh, L, LP, N, G;
     FftShape shape;
 };
@@ -481,6 +484,9 @@ struct InvArgs {
                                // value, grid holds u and becomes u v, grid2
                                // holds v and becomes u v w
     T* grid2;                  // second grid of the products (else null)
+    const V* shiftph;          // rows shifted by half a spacing: e^{-i pi m / I_j} (else null)
+    const V* chirp;            // Bluestein rows: e^{-i pi n^2 / L}
+    const V* dft;              // Bluestein rows: DFT of the conjugate chirp / L2
     int F, J, Jh, I, L, LP, N, G;
     FftShape shape;
 };
@@ -515,8 +521,53 @@ template <typename T, int LT>
 __device__ __forceinline__ int rev_of(int k, const int* rev) {
     if constexpr (LT > 0)
         return rev_fixed<T, LT>(k);
+    else if constexpr (LT == -2)
+        return k;   // Bluestein rows end in natural order
     else
         return rev[k];
+}
+
+// Bluestein's chirp-z DFT of each of nrows padded rows of half-length L (any
+// L; natural order in and out), for the rows of reduced grids whose L has a
+// prime factor above 5.  With c_n = e^{-i pi n^2 / L},
+//   Z_k = sum_n z_n e^{-2 pi i n k / L} = c_k sum_n (z_n c_n) conj(c_{k-n}),
+// a circular convolution of length L2 >= 2L - 1 (sh2.L, 2-3-5-smooth) of
+// a_n = z_n c_n (zero-padded) with the conjugate chirp wrapped around L2,
+// whose DFT D (divided by L2) is a table.  Per row: the FFT of a, the
+// pointwise product with D, conjugated and moved to natural order, a second
+// FFT, and Z_k = c_k conj(result at k).  b1, b2: two padded scratch rows of
+// length L2; tws: the per-pass twiddles of length L2; rev2: its digit
+// reversal.
+template <typename T>
+__device__ void bluestein_rows(typename Vec2<T>::type* rows, int nrows, int LP, int L,
+                               const FftShape& sh2, const typename Vec2<T>::type* tws,
+                               const typename Vec2<T>::type* chirp,
+                               const typename Vec2<T>::type* dft, const int* rev2,
+                               typename Vec2<T>::type* b1, typename Vec2<T>::type* b2) {
+    using V = typename Vec2<T>::type;
+    using K = C2<T>;
+    const int L2 = sh2.L;
+    const int tid = threadIdx.x;
+    for (int r = 0; r < nrows; ++r) {
+        V* z = rows + (size_t)r * LP;
+        for (int n = tid; n < L2; n += NT)
+            b1[ph<T>(n)] = n < L ? K::mul(z[ph<T>(n)], chirp[n]) : K::make((T)0, (T)0);
+        __syncthreads();
+        passes_runtime<T, false>(b1, 1, 0, sh2, tws);
+        for (int k = tid; k < L2; k += NT)
+            b2[ph<T>(k)] = K::conj(K::mul(b1[ph<T>(rev2[k])], dft[k]));
+        __syncthreads();
+        passes_runtime<T, false>(b2, 1, 0, sh2, tws);
+        for (int k = tid; k < L; k += NT)
+            z[ph<T>(k)] = K::mul(chirp[k], K::conj(b2[ph<T>(rev2[k])]));
+        __syncthreads();
+    }
+}
+
+// Padded pitch of a row of n complex values (fft_row_pitch on the device).
+template <typename T>
+__device__ __forceinline__ int row_pitch(int n) {
+    return n + (n >> PadShift<T>::value) + 1;
 }
 
 // Iterates idx = tid, tid + NT, ... as (major, minor) = (idx / d, idx % d)
@@ -627,7 +678,13 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             cp_async_wait_all();
         }
         __syncthreads();
-        run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
+        if constexpr (LT == -2) {
+            V* b1 = tws + A.shape.L + (2 * A.G * 4 + sizeof(V) - 1) / sizeof(V);
+            V* b2 = b1 + row_pitch<T>(A.shape.L);
+            bluestein_rows<T>(rows, nrows, LP, L, A.shape, tws, A.chirp, A.dft, A.rev, b1, b2);
+        } else {
+            run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
+        }
     }
 
     const int nout = (A.N + 1) * nf;
@@ -636,7 +693,8 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     // gathered per thread while its field stays the same, then per CTA in
     // shared memory, then one global atomic per column and CTA
     const bool track = A.colmax != nullptr;
-    unsigned* smax = reinterpret_cast<unsigned*>(tws + (LT > 0 ? LT : A.L));
+    unsigned* smax = reinterpret_cast<unsigned*>(
+        tws + (LT > 0 ? LT : (LT == -2 ? A.shape.L : A.L)));
     if (track) {
         for (int e = tid; e < 2 * nf; e += NT) smax[e] = 0u;
         __syncthreads();
@@ -714,6 +772,14 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
                 Ab = K::sub(xbn, xbs);
             }
             V osa = K::scale(Sa, sca), oaa = K::scale(Aa, sca);
+            if constexpr (RAG) {
+                // rows shifted by half a spacing: X^m e^{-i pi m / I_j}
+                if (A.shiftph) {
+                    const V pa = A.shiftph[ra];
+                    osa = K::mul(osa, pa);
+                    oaa = K::mul(oaa, pa);
+                }
+            }
             if (ra != ma) osa = oaa = K::make((T)0, (T)0);
             const size_t basea = ((size_t)ma * 2 * A.Jh + jh) * A.F + f0 + fa;
             A.work[basea] = osa;
@@ -721,6 +787,13 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             if (track) record(fa, osa, oaa);
             if (hb) {
                 V osb = K::scale(Sb, scb), oab = K::scale(Ab, scb);
+                if constexpr (RAG) {
+                    if (A.shiftph) {
+                        const V pb = A.shiftph[rb];
+                        osb = K::mul(osb, pb);
+                        oab = K::mul(oab, pb);
+                    }
+                }
                 if (rb != mb) osb = oab = K::make((T)0, (T)0);
                 const size_t baseb = ((size_t)mb * 2 * A.Jh + jh) * A.F + f0 + fb;
                 A.work[baseb] = osb;
@@ -729,10 +802,63 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
             }
         }
     };
-    if (LT <= 0 || A.rowoff)
-        out_loop(std::true_type{});
-    else
-        out_loop(std::false_type{});
+    // The two-pass FP32 lengths L = Q x 32 on regular grids: each thread keeps
+    // one field and walks the wavenumbers m = g, g + D, ... (D = NT / nf
+    // thread groups), with the digit-reversed positions tracked as the
+    // mixed-radix digits of m (m = k1 + Q k2 sits at 32 k1 + k2, padded
+    // 33 k1 + k2; L - m at the digits of its complement) and the workspace
+    // address advanced by a constant, so the loop needs no division.
+    // Consecutive threads write consecutive fields of one m, as above.
+    auto out_walk = [&]() {
+        constexpr FftShape FS = FacOf<(LT > 0 ? LT : 64), false>::v;
+        constexpr int Q = FS.radix[0];
+        const int D = NT / nf;
+        const int g = tid / nf, fl = tid - g * nf;
+        if (g >= D) return;
+        const V* zn = rows + (size_t)fl * LP;
+        const V* zs = zn + (size_t)nf * LP;
+        int k1 = g % Q, k2 = g / Q;
+        const int d1 = D % Q, d2 = D / Q;
+        V* wp = A.work + ((size_t)g * 2 * A.Jh + jh) * A.F + f0 + fl;
+        const size_t wstep = (size_t)D * 2 * A.Jh * A.F;
+        const size_t astep = (size_t)A.Jh * A.F;
+        for (int m = g; m <= A.N; m += D) {
+            const int c1 = k1 == 0 ? 0 : Q - k1;
+            const int c2 = k1 == 0 ? ((32 - k2) & 31) : 31 - k2;
+            const int pm = 33 * k1 + k2, pc = 33 * c1 + c2;
+            const V wt = A.twpost[m];
+            const V xn = real_spec(zn[pm], zn[pc], wt);
+            V S = xn, Aq = K::make((T)0, (T)0);
+            if (!equator) {
+                const V xs = real_spec(zs[pm], zs[pc], wt);
+                S = K::add(xn, xs);
+                Aq = K::sub(xn, xs);
+            }
+            const T sc = m == 0 ? sc0 : sc1;
+            const V os = K::scale(S, sc), oa = K::scale(Aq, sc);
+            wp[0] = os;
+            wp[astep] = oa;
+            if (track) record(fl, os, oa);
+            wp += wstep;
+            k1 += d1;
+            k2 += d2;
+            if (k1 >= Q) {
+                k1 -= Q;
+                ++k2;
+            }
+        }
+    };
+    if constexpr (first_pass_from_global<T, LT>()) {
+        if (!A.rowoff)
+            out_walk();
+        else
+            out_loop(std::true_type{});
+    } else {
+        if (LT <= 0 || A.rowoff)
+            out_loop(std::true_type{});
+        else
+            out_loop(std::false_type{});
+    }
     if (track) {
         flush();
         __syncthreads();
@@ -821,10 +947,21 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
             V* zs = rows + (size_t)(nf + fl) * LP;
             // S and A at frequencies q and L - q, each read once (zero above
             // kmax; Y_L = 0 for q = 0)
-            const V Sq = hq ? zn[pq] : zero;
-            const V Aq = (hq && !equator) ? zs[pq] : zero;
-            const V Sc = hc ? zn[pc] : zero;
-            const V Ac = (hc && !equator) ? zs[pc] : zero;
+            V Sq = hq ? zn[pq] : zero;
+            V Aq = (hq && !equator) ? zs[pq] : zero;
+            V Sc = hc ? zn[pc] : zero;
+            V Ac = (hc && !equator) ? zs[pc] : zero;
+            if (A.shiftph) {
+                // rows shifted by half a spacing: Y^m e^{+i pi m / I_j}
+                const V cq = K::conj(A.shiftph[q]);
+                Sq = K::mul(Sq, cq);
+                Aq = K::mul(Aq, cq);
+                if (hc) {
+                    const V cc = K::conj(A.shiftph[qc]);
+                    Sc = K::mul(Sc, cc);
+                    Ac = K::mul(Ac, cc);
+                }
+            }
             V ynq = K::scale(K::add(Sq, Aq), fq), ysq = K::scale(K::sub(Sq, Aq), fq);
             if (q == 0) ynq.y = ysq.y = (T)0;
             const V ync = K::scale(K::add(Sc, Ac), fc), ysc = K::scale(K::sub(Sc, Ac), fc);
@@ -836,15 +973,76 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
             }
         }
     };
+    // When the spectrum stops below L/2 (kmax < L/2, i.e. I > 4 kmax, true of
+    // every grid with I = 4 (N+1)), Y vanishes at L - q for all q <= L/2, so
+    // each packed value depends on one Y:
+    //   conj Z_q     = conj(Y_q) (1 - i W_I^q),
+    //   conj Z_{L-q} = Y_q (1 + i W_I^{L-q}),
+    // with the m >= 1 factor folded into the two constants, and both
+    // hemispheres' Y = S +- A formed once per field.
+    auto pack_q_short = [&](int q, V tq, V tc) {
+        const int qc = L - q;
+        const int pq = ph<T>(q), pc = ph<T>(qc);
+        const bool pair = q != 0 && q != qc;
+        const V zero = K::make((T)0, (T)0);
+        const T fq = q == 0 ? (T)1 : mf1;
+        const V al = K::make(fq * ((T)1 + tq.y), -fq * tq.x);    // f (1 - i W^q)
+        const V be = K::make(mf1 * ((T)1 - tc.y), mf1 * tc.x);   // f (1 + i W^{L-q})
+        if (q > kmax) {
+            for (int fl = 0; fl < nf; ++fl) {
+                V* zn = rows + (size_t)fl * LP;
+                V* zs = rows + (size_t)(nf + fl) * LP;
+                zn[pq] = zero;
+                if (!equator) zs[pq] = zero;
+                if (pair) {
+                    zn[pc] = zero;
+                    if (!equator) zs[pc] = zero;
+                }
+            }
+            return;
+        }
+        const V cs = A.shiftph ? K::conj(A.shiftph[q]) : K::make((T)1, (T)0);
+        for (int fl = 0; fl < nf; ++fl) {
+            V* zn = rows + (size_t)fl * LP;
+            V* zs = rows + (size_t)(nf + fl) * LP;
+            V Sq = zn[pq];
+            V Aq = equator ? zero : zs[pq];
+            if (A.shiftph) {
+                Sq = K::mul(Sq, cs);
+                Aq = K::mul(Aq, cs);
+            }
+            V yn = K::add(Sq, Aq), ys = K::sub(Sq, Aq);
+            if (q == 0) yn.y = ys.y = (T)0;
+            zn[pq] = K::mul(K::conj(yn), al);
+            if (!equator) zs[pq] = K::mul(K::conj(ys), al);
+            if (pair) {
+                zn[pc] = K::mul(yn, be);
+                if (!equator) zs[pc] = K::mul(ys, be);
+            }
+        }
+    };
+    const bool short_spec = 2 * kmax < L;
     if constexpr (LT > 0) {
+        if (short_spec) {
 #pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-            const int q = tid + i * NT;
-            if (q <= half) pack_q(q, twq[i], twc[i]);
+            for (int i = 0; i < NQ; ++i) {
+                const int q = tid + i * NT;
+                if (q <= half) pack_q_short(q, twq[i], twc[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NQ; ++i) {
+                const int q = tid + i * NT;
+                if (q <= half) pack_q(q, twq[i], twc[i]);
+            }
         }
     } else {
-        for (int q = tid; q <= half; q += NT)
-            pack_q(q, A.twpost[q], A.twpost[q == 0 ? 0 : L - q]);
+        for (int q = tid; q <= half; q += NT) {
+            if (short_spec)
+                pack_q_short(q, A.twpost[q], A.twpost[q == 0 ? 0 : L - q]);
+            else
+                pack_q(q, A.twpost[q], A.twpost[q == 0 ? 0 : L - q]);
+        }
     }
     __syncthreads();
     if constexpr (inverse_stores_from_last_pass<T, LT>()) {
@@ -893,7 +1091,13 @@ __device__ __forceinline__ void inv_body(const InvArgs<T>& A, int fg, int jh) {
             last_pass(std::integral_constant<int, 0>{});
         return;
     }
-    run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
+    if constexpr (LT == -2) {
+        V* b1 = tws + A.shape.L;
+        V* b2 = b1 + row_pitch<T>(A.shape.L);
+        bluestein_rows<T>(rows, nrows, LP, L, A.shape, tws, A.chirp, A.dft, A.rev, b1, b2);
+    } else {
+        run_passes<T, LT>(rows, nrows, LP, A.shape, tws);
+    }
 
     // store of one synthesised pair of values y at xv[k] (x2: the second
     // grid of the products)
@@ -1013,25 +1217,46 @@ template <typename T> struct RaggedFwd {
     FwdArgs<T> a;
     const RShape* shapes;
     const int* shape_of;
+    const int* shift_of;                       // per latitude pair (null: none shifted)
+    const typename Vec2<T>::type* shiftbase;   // all shapes' shift phases
+    const typename Vec2<T>::type* chirpbase;   // all Bluestein shapes' chirps
+    const typename Vec2<T>::type* dftbase;     // all Bluestein shapes' chirp spectra
 };
 
 template <typename T> struct RaggedInv {
     InvArgs<T> a;
     const RShape* shapes;
     const int* shape_of;
+    const int* shift_of;
+    const typename Vec2<T>::type* shiftbase;
+    const typename Vec2<T>::type* chirpbase;
+    const typename Vec2<T>::type* dftbase;
 };
+
+// Per-CTA arguments of a reduced-grid row class: the latitude pair's shape,
+// its tables, and its shift.
+template <typename Args, typename R>
+__device__ __forceinline__ void apply_shape(Args& A, const R& Rg, int jh) {
+    const RShape& rs = Rg.shapes[Rg.shape_of[jh]];
+    A.shape = rs.sh;
+    A.L = rs.L;
+    A.twp += rs.tw_off;
+    A.twpost += rs.post_off;
+    A.rev += rs.rev_off;
+    A.shiftph = (Rg.shift_of && Rg.shift_of[jh] && rs.shift_off >= 0)
+                    ? Rg.shiftbase + rs.shift_off : nullptr;
+    if (rs.bluestein) {
+        A.chirp = Rg.chirpbase + rs.chirp_off;
+        A.dft = Rg.dftbase + rs.dft_off;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_forward_ragged_kernel(const __grid_constant__ RaggedFwd<T> R) {
     const int jh = R.a.jh_list[blockIdx.y];
-    const RShape& rs = R.shapes[R.shape_of[jh]];
     FwdArgs<T> A = R.a;
-    A.shape = rs.sh;
-    A.L = rs.sh.L;
-    A.twp += rs.tw_off;
-    A.twpost += rs.post_off;
-    A.rev += rs.rev_off;
+    apply_shape(A, R, jh);
     fwd_body<T, -1, false>(A, blockIdx.x, jh);
 }
 
@@ -1039,14 +1264,28 @@ template <typename T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     fft_inverse_ragged_kernel(const __grid_constant__ RaggedInv<T> R) {
     const int jh = R.a.jh_list[blockIdx.y];
-    const RShape& rs = R.shapes[R.shape_of[jh]];
     InvArgs<T> A = R.a;
-    A.shape = rs.sh;
-    A.L = rs.sh.L;
-    A.twp += rs.tw_off;
-    A.twpost += rs.post_off;
-    A.rev += rs.rev_off;
+    apply_shape(A, R, jh);
     inv_body<T, -1>(A, blockIdx.x, jh);
+}
+
+// Rows whose half-length has a prime factor above 5: Bluestein's method.
+template <typename T>
+__global__ void __launch_bounds__(NT, 1)
+    fft_forward_bluestein_kernel(const __grid_constant__ RaggedFwd<T> R) {
+    const int jh = R.a.jh_list[blockIdx.y];
+    FwdArgs<T> A = R.a;
+    apply_shape(A, R, jh);
+    fwd_body<T, -2, false>(A, blockIdx.x, jh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 1)
+    fft_inverse_bluestein_kernel(const __grid_constant__ RaggedInv<T> R) {
+    const int jh = R.a.jh_list[blockIdx.y];
+    InvArgs<T> A = R.a;
+    apply_shape(A, R, jh);
+    inv_body<T, -2>(A, blockIdx.x, jh);
 }
 
 template <typename T, int LT>
@@ -1113,6 +1352,7 @@ FwdArgs<T> make_fwd_args(const sht_plan_s* p, const void* grid, const RowSource&
     A.colmax = p->d_colmax;
     A.rowoff = nullptr;
     A.jh_list = nullptr;
+    A.shiftph = A.chirp = A.dft = nullptr;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.L = p->fft.L; A.N = p->N; A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
     A.shape = p->fft;
@@ -1152,6 +1392,7 @@ InvArgs<T> make_inv_args(const sht_plan_s* p, const void* work, const InvScale& 
     A.jh_list = nullptr;
     A.accumulate = sc.accumulate;
     A.grid2 = static_cast<T*>(sc.grid2);
+    A.shiftph = A.chirp = A.dft = nullptr;
     A.F = p->F; A.J = p->J; A.Jh = p->Jh; A.I = p->I; A.L = p->fft.L; A.N = p->N;
     A.G = p->G;
     A.LP = fft_row_pitch(p->fft.L, sizeof(T) == 8);
@@ -1240,20 +1481,37 @@ cudaError_t fwd_ragged_impl(const sht_plan_s* p, const void* grid, const FwdScal
                                                   fft_smem_bytes(2 * A.L, p->G, vb == 16), s);
         if (e) return e;
     }
-    if (rg->generic_count == 0) return cudaSuccess;
     RaggedFwd<T> R;
     R.a = base;
     R.a.twp = static_cast<const V*>(rg->d_twpass);
     R.a.twpost = static_cast<const V*>(rg->d_twpost);
     R.a.rev = rg->d_rev;
-    R.a.jh_list = rg->d_jh + rg->generic_off;
     R.shapes = rg->d_shapes;
     R.shape_of = rg->d_shape_of;
-    cudaError_t e = ensure_smem((const void*)fft_forward_ragged_kernel<T>, p->fft_smem);
-    if (e) return e;
-    fft_forward_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
-    note_launch();
-    return cudaGetLastError();
+    R.shift_of = rg->any_shift ? rg->d_shift_of : nullptr;
+    R.shiftbase = static_cast<const V*>(rg->d_shiftph);
+    R.chirpbase = static_cast<const V*>(rg->d_chirp);
+    R.dftbase = static_cast<const V*>(rg->d_dft);
+    cudaError_t e;
+    if (rg->generic_count > 0) {
+        R.a.jh_list = rg->d_jh + rg->generic_off;
+        e = ensure_smem((const void*)fft_forward_ragged_kernel<T>, p->fft_smem);
+        if (e) return e;
+        fft_forward_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
+        note_launch();
+        if ((e = cudaGetLastError())) return e;
+    }
+    if (rg->blue_count > 0) {
+        R.a.jh_list = rg->d_jh + rg->blue_off;
+        R.a.G = rg->blue_G;
+        const unsigned nfb = (p->F + rg->blue_G - 1) / rg->blue_G;
+        e = ensure_smem((const void*)fft_forward_bluestein_kernel<T>, rg->blue_smem);
+        if (e) return e;
+        fft_forward_bluestein_kernel<T><<<dim3(nfb, rg->blue_count), NT, rg->blue_smem, s>>>(R);
+        note_launch();
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -1273,20 +1531,37 @@ cudaError_t inv_ragged_impl(const sht_plan_s* p, const void* work, const InvScal
                                                   fft_smem_bytes(2 * A.L, p->G, vb == 16), s);
         if (e) return e;
     }
-    if (rg->generic_count == 0) return cudaSuccess;
     RaggedInv<T> R;
     R.a = base;
     R.a.twp = static_cast<const V*>(rg->d_twpass);
     R.a.twpost = static_cast<const V*>(rg->d_twpost);
     R.a.rev = rg->d_rev;
-    R.a.jh_list = rg->d_jh + rg->generic_off;
     R.shapes = rg->d_shapes;
     R.shape_of = rg->d_shape_of;
-    cudaError_t e = ensure_smem((const void*)fft_inverse_ragged_kernel<T>, p->fft_smem);
-    if (e) return e;
-    fft_inverse_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
-    note_launch();
-    return cudaGetLastError();
+    R.shift_of = rg->any_shift ? rg->d_shift_of : nullptr;
+    R.shiftbase = static_cast<const V*>(rg->d_shiftph);
+    R.chirpbase = static_cast<const V*>(rg->d_chirp);
+    R.dftbase = static_cast<const V*>(rg->d_dft);
+    cudaError_t e;
+    if (rg->generic_count > 0) {
+        R.a.jh_list = rg->d_jh + rg->generic_off;
+        e = ensure_smem((const void*)fft_inverse_ragged_kernel<T>, p->fft_smem);
+        if (e) return e;
+        fft_inverse_ragged_kernel<T><<<dim3(nfg, rg->generic_count), NT, p->fft_smem, s>>>(R);
+        note_launch();
+        if ((e = cudaGetLastError())) return e;
+    }
+    if (rg->blue_count > 0) {
+        R.a.jh_list = rg->d_jh + rg->blue_off;
+        R.a.G = rg->blue_G;
+        const unsigned nfb = (p->F + rg->blue_G - 1) / rg->blue_G;
+        e = ensure_smem((const void*)fft_inverse_bluestein_kernel<T>, rg->blue_smem);
+        if (e) return e;
+        fft_inverse_bluestein_kernel<T><<<dim3(nfb, rg->blue_count), NT, rg->blue_smem, s>>>(R);
+        note_launch();
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -1381,6 +1656,14 @@ cudaError_t launch_fft_inverse_group(sht_plan_s* const* plans, int n,
                                      void* const* grids, cudaStream_t s) {
     if (plans[0]->prec == SHT_FP64) return inv_group_impl<double>(plans, n, grids, s);
     return inv_group_impl<float>(plans, n, grids, s);
+}
+
+size_t bluestein_smem_bytes(int Lmax, int L2, int G, bool fp64) {
+    const size_t v = fp64 ? sizeof(double2) : sizeof(float2);
+    // rows | twiddles of length L2 | column maxima (2 G words, rounded up to
+    // whole complex values) | two scratch rows of length L2
+    return (2 * (size_t)G * fft_row_pitch(Lmax, fp64) + L2 + (8 * (size_t)G + v - 1) / v +
+            2 * (size_t)fft_row_pitch(L2, fp64)) * v;
 }
 
 size_t fft_smem_bytes(int I, int G, bool fp64) {

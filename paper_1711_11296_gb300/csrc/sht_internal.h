@@ -83,10 +83,16 @@ struct SplitTables;   // tensor-core operand tables (split plans)
 // distinct half-lengths L = I_j/2 each have an FFT shape and tables; their
 // tables are concatenated in device buffers at the offsets below.
 struct RShape {
-    FftShape sh;
+    FftShape sh;          // the passes: of L, or of L2 for a Bluestein shape
     long long tw_off;     // per-pass twiddle tables (entries)
     long long post_off;   // e^{-2 pi i q / I_j}, q < L (entries)
-    long long rev_off;    // digit-reversed positions (entries)
+    long long rev_off;    // digit-reversed positions of the passes' length (entries)
+    int L = 0;            // half-length of the rows, L = I_j / 2
+    int bluestein = 0;    // 1: L has a prime factor above 5; its DFT is a
+                          // chirp-z convolution of length L2 = sh.L >= 2L - 1
+    long long chirp_off = 0;   // Bluestein: e^{-pi i n^2 / L}, n < L (entries)
+    long long dft_off = 0;     // Bluestein: DFT of the conjugate chirp / L2 (L2 entries)
+    long long shift_off = -1;  // e^{-pi i m / I_j}, m < L (entries), or -1: none
 };
 
 struct RaggedGrid {
@@ -94,19 +100,35 @@ struct RaggedGrid {
     long long npts = 0;              // grid points per field (sum of I_j)
     long long* d_rowoff = nullptr;   // [J] first point of row j within a field
     int* d_shape_of = nullptr;       // [Jh] shape index of latitude pair jh
+    int* d_shift_of = nullptr;       // [Jh] 1: the pair's longitudes are shifted by
+                                     // half a spacing (lambda_i = 2 pi (i + 1/2) / I_j)
     RShape* d_shapes = nullptr;      // [nshapes]
     void* d_twpass = nullptr;        // all shapes' per-pass twiddle tables
     void* d_twpost = nullptr;        // all shapes' real-spectrum twiddles
     int* d_rev = nullptr;            // all shapes' digit reversals
+    void* d_chirp = nullptr;         // Bluestein shapes' chirps
+    void* d_dft = nullptr;           // Bluestein shapes' chirp spectra
+    void* d_shiftph = nullptr;       // phase tables of the shifted rows' shapes
     int nshapes = 0;
+    bool any_shift = false;
     // Latitude pairs by launch: one launch per half-length that has a
-    // compile-time FFT kernel (classes), one generic launch for the rest.
+    // compile-time FFT kernel (classes, unshifted rows), one generic launch
+    // for the other 2-3-5-smooth rows and one Bluestein launch for the rows
+    // whose half-length has a larger prime factor.
     struct Class { int shape; int off; int count; };
     std::vector<Class> classes;
     std::vector<RShape> h_shapes;    // host copy of d_shapes
     int generic_off = 0, generic_count = 0;
+    int blue_off = 0, blue_count = 0;
+    int blue_G = 1;                  // fields per CTA of the Bluestein launch
+    size_t blue_smem = 0;            // its dynamic shared memory
     int* d_jh = nullptr;             // latitude-pair lists of all launches
 };
+
+// Shared memory of the Bluestein FFT kernels: the padded rows of G fields
+// (pitch of half-length Lmax), the per-pass twiddles of length L2, the
+// column maxima and two padded scratch rows of length L2.
+size_t bluestein_smem_bytes(int Lmax, int L2, int G, bool fp64);
 
 // Half-lengths with compile-time FFT kernels (the standard grids).
 inline bool fft_has_fixed_kernel(int L) {
@@ -202,6 +224,17 @@ cudaError_t build_twiddles(sht_plan_s* p, cudaStream_t s);
 cudaError_t launch_twpass(const sht_plan_s* p, cudaStream_t s);
 cudaError_t build_fft_tables(const FftShape& sh, bool fp64, void* twpass, void* twpost,
                              int* rev, void* tmp, cudaStream_t s);
+// Tables of a Bluestein shape (rows of half-length L, passes sh2 of length
+// L2 >= 2L - 1): the passes' twiddles and digit reversal, the row's
+// real-spectrum twiddles e^{-2 pi i q / 2L}, the chirp e^{-pi i n^2 / L}
+// (n < L) and the DFT of length L2 of the conjugate chirp wrapped around
+// L2, divided by L2.  tmp: device scratch of 4 L2 doubles.
+cudaError_t build_bluestein_tables(int L, const FftShape& sh2, bool fp64, void* twpass,
+                                   void* twpost, int* rev, void* chirp, void* dft, void* tmp,
+                                   cudaStream_t s);
+// e^{-pi i m / I} for m < n (the zonal phase of a row shifted by half a
+// spacing), in the plan's precision.
+cudaError_t build_shift_table(int n, int I, bool fp64, void* out, cudaStream_t s);
 void ragged_free(RaggedGrid* rg);
 int inverse_scaled(sht_plan_s* p, const void* spec, const InvScale& sc, void* grid,
                    cudaStream_t s);

@@ -268,6 +268,107 @@ cudaError_t build_fft_tables(const FftShape& sh, bool fp64, void* twpass, void* 
     return cudaStreamSynchronize(s);
 }
 
+namespace {
+
+// c_n = e^{-pi i n^2 / L}, the angle reduced exactly as (n^2 mod 2L) / L.
+template <typename V>
+__global__ void chirp_kernel(V* out, double2* out64, int L) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L) return;
+    const long long r = ((long long)n * n) % (2LL * L);
+    double sn, cs;
+    sincospi((double)r / (double)L, &sn, &cs);
+    V v;
+    v.x = cs;
+    v.y = -sn;
+    out[n] = v;
+    out64[n] = make_double2(cs, -sn);
+}
+
+// cos(2 pi r / n), r < n.
+__global__ void cos_table_kernel(double* out, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) out[r] = cospi(2.0 * (double)r / (double)n);
+}
+
+// D_k = (1/L2) sum_j b_j e^{-2 pi i j k / L2} for the conjugate chirp b
+// wrapped around L2 (b_j = conj c_j for 0 <= j < L, b_{L2-j} = conj c_j for
+// 0 < j < L, zero between): D_k = (1/L2) (1 + 2 sum_{0<j<L} conj(c_j)
+// cos(2 pi j k / L2)), a direct FP64 sum with j k reduced mod L2 exactly.
+template <typename V>
+__global__ void bluestein_dft_kernel(V* out, const double2* c, const double* costab, int L,
+                                     int L2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L2) return;
+    double re = 1.0, im = 0.0;
+    int r = 0;
+    for (int j = 1; j < L; ++j) {
+        r += k;
+        if (r >= L2) r -= L2;
+        const double cw = 2.0 * costab[r];
+        re = fma(c[j].x, cw, re);
+        im = fma(-c[j].y, cw, im);
+    }
+    V v;
+    v.x = re / (double)L2;
+    v.y = im / (double)L2;
+    out[k] = v;
+}
+
+template <typename V>
+__global__ void shift_kernel(V* out, int n, int I) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    double sn, cs;
+    sincospi((double)m / (double)I, &sn, &cs);
+    V v;
+    v.x = cs;
+    v.y = -sn;
+    out[m] = v;
+}
+
+}  // namespace
+
+cudaError_t build_bluestein_tables(int L, const FftShape& sh2, bool fp64, void* twpass,
+                                   void* twpost, int* rev, void* chirp, void* dft, void* tmp,
+                                   cudaStream_t s) {
+    const int L2 = sh2.L;
+    const int threads = 128;
+    // scratch: L2 entries for the passes' base twiddles, L2 for their unused
+    // real-spectrum twiddles, then the FP64 chirp (L) and cosine table (L2)
+    char* t = static_cast<char*>(tmp);
+    const size_t vb = fp64 ? sizeof(double2) : sizeof(float2);
+    void* base = t;
+    void* post2 = t + L2 * vb;
+    double2* c64 = reinterpret_cast<double2*>(t + 2 * L2 * sizeof(double2));
+    double* costab = reinterpret_cast<double*>(c64 + L2);
+    cudaError_t e = build_fft_tables(sh2, fp64, twpass, post2, rev, base, s);
+    if (e != cudaSuccess) return e;
+    const int bL = (L + threads - 1) / threads, bL2 = (L2 + threads - 1) / threads;
+    cos_table_kernel<<<bL2, threads, 0, s>>>(costab, L2);
+    if (fp64) {
+        twiddle_kernel<double2><<<bL, threads, 0, s>>>((double2*)twpost, L, 2 * L);
+        chirp_kernel<double2><<<bL, threads, 0, s>>>((double2*)chirp, c64, L);
+        bluestein_dft_kernel<double2><<<bL2, threads, 0, s>>>((double2*)dft, c64, costab, L, L2);
+    } else {
+        twiddle_kernel<float2><<<bL, threads, 0, s>>>((float2*)twpost, L, 2 * L);
+        chirp_kernel<float2><<<bL, threads, 0, s>>>((float2*)chirp, c64, L);
+        bluestein_dft_kernel<float2><<<bL2, threads, 0, s>>>((float2*)dft, c64, costab, L, L2);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t build_shift_table(int n, int I, bool fp64, void* out, cudaStream_t s) {
+    const int threads = 128, blocks = (n + threads - 1) / threads;
+    if (fp64)
+        shift_kernel<double2><<<blocks, threads, 0, s>>>((double2*)out, n, I);
+    else
+        shift_kernel<float2><<<blocks, threads, 0, s>>>((float2*)out, n, I);
+    return cudaGetLastError();
+}
+
 }  // namespace sht
 
 namespace sht {

@@ -30,13 +30,15 @@ class Plan:
     tensors, split plans float32/complex64."""
 
     def __init__(self, N, J, I, nfields, precision="fp64", device=None, grid="cc",
-                 lat_points=None):
+                 lat_points=None, half_shift=None):
         if precision not in PRECISION:
             raise ValueError("precision must be one of %s" % list(PRECISION))
         if grid not in _native.GRID and grid != "reduced":
             raise ValueError("grid must be one of %s" % (list(_native.GRID) + ["reduced"]))
         if (grid == "reduced") != (lat_points is not None):
             raise ValueError("lat_points goes with grid='reduced' and only with it")
+        if half_shift is not None and grid != "reduced":
+            raise ValueError("half_shift goes with grid='reduced'")
         self.grid = grid
         self.device = torch.device("cuda", torch.cuda.current_device()
                                    if device is None else torch.device(device).index or 0)
@@ -52,14 +54,25 @@ class Plan:
                 if len(pts) != J:
                     raise ValueError("lat_points needs J = %d entries" % J)
                 arr = (ctypes.c_int * J)(*pts)
-                rc = check(lib.sht_plan_create_reduced(N, J, arr, nfields,
-                                                       PRECISION[precision], ctypes.byref(h)))
+                if half_shift is None:
+                    rc = check(lib.sht_plan_create_reduced(N, J, arr, nfields,
+                                                           PRECISION[precision],
+                                                           ctypes.byref(h)))
+                else:
+                    sh = [int(v) for v in half_shift]
+                    if len(sh) != J:
+                        raise ValueError("half_shift needs J = %d entries" % J)
+                    rc = check(lib.sht_plan_create_reduced_shifted(
+                        N, J, arr, (ctypes.c_int * J)(*sh), nfields, PRECISION[precision],
+                        ctypes.byref(h)))
+                self.half_shift = None if half_shift is None else [int(v) for v in half_shift]
                 self.lat_points = pts
                 self.I = max(pts)
             else:
                 rc = check(lib.sht_plan_create_grid(N, J, I, nfields, PRECISION[precision],
                                                     _native.GRID[grid], ctypes.byref(h)))
                 self.lat_points = None
+                self.half_shift = None
         self.exact = rc == _native.SHT_OK
         self._h = h
         npts = ctypes.c_longlong()
@@ -321,6 +334,23 @@ class Group:
             pass
 
 
+def octahedral_grid_sizes(J, first=20, step=4):
+    """Longitudes per latitude of the octahedral Clenshaw-Curtis grid
+    (Sec. 6): first + step (j - 1) on the j-th latitude from either pole."""
+    out = (ctypes.c_int * J)()
+    check(lib.sht_octahedral_grid_sizes(J, first, step, out))
+    return list(out)
+
+
+def icositetrahedral_grid_sizes(J):
+    """(longitudes per latitude, half-spacing shift per latitude) of the
+    icositetrahedral Clenshaw-Curtis grid (Sec. 6), for
+    ``Plan(..., grid="reduced", lat_points=..., half_shift=...)``."""
+    pts, sh = (ctypes.c_int * J)(), (ctypes.c_int * J)()
+    check(lib.sht_icositetrahedral_grid_sizes(J, pts, sh))
+    return list(pts), list(sh)
+
+
 class Analysis(torch.autograd.Function):
     """grid -> spectrum with the native adjoint as backward."""
 
@@ -356,4 +386,4 @@ def synthesis(spec, plan):
 
 
 __all__ = ["Plan", "Group", "Analysis", "Synthesis", "analysis", "synthesis",
-           "SHTError"]
+           "octahedral_grid_sizes", "icositetrahedral_grid_sizes", "SHTError"]

@@ -78,7 +78,6 @@ def _lat(pts):
     (15, 8, [32] * 8),                              # J even
     (15, 7, [16, 24, 32, 40, 32, 24, 18]),          # not symmetric
     (15, 7, [16, 25, 32, 40, 32, 25, 16]),          # odd count
-    (15, 7, [14, 24, 32, 40, 32, 24, 14]),          # 14/2 = 7: not 2-3-5 smooth
     (15, 7, [16, 24, 32, 16384, 32, 24, 16]),       # count above 8192
     (15, 7, [16, 24, 30, 30, 30, 24, 16]),          # widest row does not exceed 2N
 ])
@@ -105,3 +104,42 @@ def test_newer_entry_points_reject_null_handles(lib):
     assert lib.sht_plan_grid_points(None, buf) == -6
     assert lib.sht_profile_read_kernels(None, buf, buf, buf) == -6
     assert lib.sht_prolong_spectral_add(None, buf, 0, buf, None) == -6
+
+
+@pytest.mark.parametrize("shift", [
+    [0, 0, 2, 0, 2, 0, 0],                          # not 0 or 1
+    [0, 1, 0, 0, 0, 0, 0],                          # not symmetric
+])
+def test_invalid_shifts_rejected_on_host(lib, shift):
+    h = ctypes.c_void_p()
+    vp = ctypes.c_void_p
+    lib.sht_plan_create_reduced_shifted.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp,
+                                                    ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(vp)]
+    pts = [16, 24, 32, 40, 32, 24, 16]
+    assert lib.sht_plan_create_reduced_shifted(15, 7, ctypes.cast(_lat(pts), vp),
+                                               ctypes.cast(_lat(shift), vp), 1, 0,
+                                               ctypes.byref(h)) == -1
+    assert not h.value
+    assert lib.sht_plan_create_reduced_shifted(15, 7, ctypes.cast(_lat(pts), vp), None, 1, 0,
+                                               ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("J", [1, 9, 47, 1281])
+def test_octahedral_and_icositetrahedral_counts_match_the_oracle(lib, J):
+    # host-only entry points against the oracle's own restatement
+    import oracle as O
+    buf = (ctypes.c_int * J)()
+    lib.sht_octahedral_grid_sizes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_void_p]
+    assert lib.sht_octahedral_grid_sizes(J, 20, 4, buf) == 0
+    assert list(buf) == O.octahedral_sizes(J).tolist()
+    sh = (ctypes.c_int * J)()
+    lib.sht_icositetrahedral_grid_sizes.argtypes = [ctypes.c_int, ctypes.c_void_p,
+                                                    ctypes.c_void_p]
+    assert lib.sht_icositetrahedral_grid_sizes(J, buf, sh) == 0
+    Ij, s = O.icositetrahedral_sizes(J)
+    assert list(buf) == Ij.tolist()
+    assert list(sh) == [int(2 * v) for v in s]
+    assert lib.sht_octahedral_grid_sizes(J + 1, 20, 4, buf) == -1
+    assert lib.sht_octahedral_grid_sizes(J, 21, 4, buf) == -1

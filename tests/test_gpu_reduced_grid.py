@@ -137,7 +137,6 @@ def test_rejected_requests(sht):
     bad = [
         pts[:-1] + [16],                           # not symmetric
         [p + 1 if p == 18 else p for p in pts],    # odd count
-        [14 if p == 18 else p for p in pts],       # 14/2 = 7 is not 2-3-5 smooth
         [min(p, 30) for p in pts],                 # the widest row does not exceed 2N
         pts[:-1],                                  # J - 1 entries
     ]
