@@ -166,10 +166,10 @@ template <typename T> struct Dft<T, 3> {
         const V t1 = K::add(a[1], a[2]), t2 = K::sub(a[1], a[2]);
         const V y0 = K::add(a[0], t1);
         const V m0 = K::make(a[0].x - (T)0.5 * t1.x, a[0].y - (T)0.5 * t1.y);
-        const V q = K::mul_mi(K::scale(t2, h));
+        // m0 -+ i h t2, component by component
         a[0] = y0;
-        a[1] = K::add(m0, q);
-        a[2] = K::sub(m0, q);
+        a[1] = K::make(m0.x + h * t2.y, m0.y - h * t2.x);
+        a[2] = K::make(m0.x - h * t2.y, m0.y + h * t2.x);
     }
 };
 
@@ -179,11 +179,12 @@ template <typename T> struct Dft<T, 4> {
     static __device__ __forceinline__ void run(V* a) {
         using K = C2<T>;
         const V s02 = K::add(a[0], a[2]), d02 = K::sub(a[0], a[2]);
-        const V s13 = K::add(a[1], a[3]), d13 = K::mul_mi(K::sub(a[1], a[3]));
+        const V s13 = K::add(a[1], a[3]), t = K::sub(a[1], a[3]);
         a[0] = K::add(s02, s13);
         a[2] = K::sub(s02, s13);
-        a[1] = K::add(d02, d13);
-        a[3] = K::sub(d02, d13);
+        // d02 -+ i t, component by component (no swapped pair)
+        a[1] = K::make(d02.x + t.y, d02.y - t.x);
+        a[3] = K::make(d02.x - t.y, d02.y + t.x);
     }
 };
 
@@ -200,14 +201,14 @@ template <typename T> struct Dft<T, 8> {
         Dft<T, 4>::run(e);
         Dft<T, 4>::run(o);
         const V o1 = K::make(r * (o[1].x + o[1].y), r * (o[1].y - o[1].x));   // W8^1 o1
-        const V o2 = K::mul_mi(o[2]);                                          // W8^2 o2
         const V o3 = K::make(r * (o[3].y - o[3].x), -r * (o[3].x + o[3].y));   // W8^3 o3
         a[0] = K::add(e[0], o[0]);
         a[4] = K::sub(e[0], o[0]);
         a[1] = K::add(e[1], o1);
         a[5] = K::sub(e[1], o1);
-        a[2] = K::add(e[2], o2);
-        a[6] = K::sub(e[2], o2);
+        // W8^2 o2 = -i o2, component by component
+        a[2] = K::make(e[2].x + o[2].y, e[2].y - o[2].x);
+        a[6] = K::make(e[2].x - o[2].y, e[2].y + o[2].x);
         a[3] = K::add(e[3], o3);
         a[7] = K::sub(e[3], o3);
     }
@@ -231,10 +232,10 @@ template <typename T> struct Dft<T, 5> {
         const V q1 = K::make(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
         const V q2 = K::make(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
         a[0] = y0;
-        a[1] = K::add(p1, K::mul_mi(q1));
-        a[4] = K::sub(p1, K::mul_mi(q1));
-        a[2] = K::add(p2, K::mul_mi(q2));
-        a[3] = K::sub(p2, K::mul_mi(q2));
+        a[1] = K::make(p1.x + q1.y, p1.y - q1.x);
+        a[4] = K::make(p1.x - q1.y, p1.y + q1.x);
+        a[2] = K::make(p2.x + q2.y, p2.y - q2.x);
+        a[3] = K::make(p2.x - q2.y, p2.y + q2.x);
     }
 };
 
@@ -718,8 +719,10 @@ __device__ __forceinline__ void fwd_body(const FwdArgs<T>& A, int fg, int jh) {
     };
     // 2 X_m = (Z_m + conj Z_{L-m}) + W_I^m (-i)(Z_m - conj Z_{L-m})
     auto real_spec = [&](V zm, V zc, V wt) -> V {
-        const V c = K::conj(zc);
-        return K::add(K::add(zm, c), K::mul(wt, K::mul_mi(K::sub(zm, c))));
+        // s = zm + conj zc, d = zm - conj zc; s + wt (-i d), componentwise
+        const T sx = zm.x + zc.x, sy = zm.y - zc.y;
+        const T dx = zm.x - zc.x, dy = zm.y + zc.y;
+        return K::make(sx + wt.x * dy + wt.y * dx, sy - wt.x * dx + wt.y * dy);
     };
     // output scales, converted once (FP64 conversions use the narrow FP64 pipe)
     const T sc0 = (T)0.5 * rs * (T)A.mscale0, sc1 = (T)0.5 * rs * (T)A.mscale1;
