@@ -310,12 +310,14 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
     constexpr int NS = CF::NS;
     constexpr int NR = CF::NR;
-    // Forward with 128-wide column tiles: the product is formed transposed,
+    // With 128-wide column tiles the product is formed transposed,
     // D^T = B^T A^T, with the 128 columns of B on the MMA's M side and the
     // tile's A rows (at most 128, rounded up to 16) on its N side, so a
     // partial row tile issues only the MMA work of its rows.  TMEM lanes are
-    // then columns and TMEM columns rows.
-    constexpr bool SWAP = !BPRE && TN == 128;
+    // then columns and TMEM columns rows, and the epilogue stores each output
+    // row as 32 adjacent columns per warp instruction (coalesced; with the
+    // rows on the lanes, every lane would write its own row).
+    constexpr bool SWAP = TN == 128;
     constexpr int NB = 3 * NS + 2 * NR + 1;   // barriers
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
