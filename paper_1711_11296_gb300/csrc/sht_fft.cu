@@ -1274,7 +1274,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 
 // Rows whose half-length has a prime factor above 5: Bluestein's method.
 template <typename T>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
     fft_forward_bluestein_kernel(const __grid_constant__ RaggedFwd<T> R) {
     const int jh = R.a.jh_list[blockIdx.y];
     FwdArgs<T> A = R.a;
@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, 2)
     fft_inverse_bluestein_kernel(const __grid_constant__ RaggedInv<T> R) {
     const int jh = R.a.jh_list[blockIdx.y];
     InvArgs<T> A = R.a;

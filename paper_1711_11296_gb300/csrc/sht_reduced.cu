@@ -196,7 +196,7 @@ int attach_ragged(sht_plan_s* p, const int* I_lat, const int* shift) {
         // fields per CTA of the Bluestein launch: as many as fit (rows at
         // the pitch of the plan's own half-length, which the kernels use)
         const int Lrow = std::max(Lmax, p->fft.L);
-        int G = std::min(4, p->F);
+        int G = std::min(1, p->F);
         while (G > 1 && bluestein_smem_bytes(Lrow, L2max, G, fp64) > 227 * 1024) --G;
         rg->blue_G = G;
         rg->blue_smem = bluestein_smem_bytes(Lrow, L2max, G, fp64);
