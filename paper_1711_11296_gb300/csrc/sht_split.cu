@@ -17,11 +17,15 @@
 // at ((i8 * TK/8) + k8) * 128 within a K-slab of TK = 16.  A 128-row tile
 // of a slab is therefore one contiguous block that one bulk asynchronous
 // copy (TMA engine, cp.async.bulk) moves into shared memory.
-// B (the FP32 Fourier data or spectrum) stays FP32 in HBM.  Its TK rows of
-// a tile arrive by bulk copies too (one per row, 16-byte aligned when the
-// field count is even; otherwise the converters load them directly), and
-// four converter warps split them into BF16 terms, stored in the same
-// K-major core-matrix layout.
+// B (the FP32 Fourier data or spectrum) stays FP32 in HBM.  The TK x TN
+// block of a tile arrives as one tiled tensor copy (cp.async.bulk.tensor
+// over the whole Fourier workspace viewed as a row-major matrix of 2F
+// columns) when the rows are 16-byte aligned (even field counts), else by
+// one bulk copy per row, else the converters load it directly.  A bulk
+// copy costs about the same SM time whatever its size, so one copy per
+// stage instead of TK keeps the copy engine from bounding the pipeline.
+// The converter warps split B into BF16 terms, stored in the same K-major
+// core-matrix layout.
 //
 // One CTA computes a 128 x 128 output tile through a 3-stage pipeline
 // (two CTAs share an SM, so one's prologue and epilogue overlap the
@@ -32,6 +36,7 @@
 // K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
 // a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
 // waits (bounded) for its MMAs and frees its tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -135,7 +140,8 @@ struct GemmArgs {
     const float* B;
     float* O;
     int C;                          // valid columns (2F)
-    int raw_bulk;                   // 1: B rows arrive by bulk copy (16-byte aligned)
+    int raw_bulk;                   // 1: B rows arrive by bulk copy (16-byte aligned),
+                                    // 2: as one tiled tensor copy per stage (bmap)
     int* status;
     const float* rs_inv;            // FP16: 1 / row scale per A row (pr.rs_off + row)
     const unsigned* colmax;         // FP16: max |B| per column (float bits)
@@ -143,6 +149,10 @@ struct GemmArgs {
     long long bplane_bytes;
     int nct;                        // column tiles (pre-split B tile index = it * nct + ct)
     int stall;                      // fault injection for tests: CTA 0 never arms stage 0
+    // raw_bulk == 2: B as a row-major matrix [rows][C] of floats (problem
+    // rows at b_off / b_stride), box TN columns x TK rows; out-of-range
+    // columns and rows read as zero
+    CUtensorMap bmap;
 };
 
 // FP16 operands are scaled by powers of two into [-1, 1): column c of B by
@@ -208,6 +218,17 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
         "[%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// One TK x TN box of the tensor map at column x, row y (x * 4 bytes is a
+// multiple of 16: x is a multiple of TN).
+__device__ __forceinline__ void tensor_g2s_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                              uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 
@@ -423,6 +444,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             const int ccopy = min(TN, g.C - cbase);   // valid columns
             const uint32_t rbytes = (uint32_t)ccopy * 4u;
             constexpr int NRS = NR > 0 ? NR : 1;
+            const bool tiled = g.raw_bulk == 2;
+            const int y0 = tiled ? (int)(pr.b_off / pr.b_stride) : 0;   // matrix row of k = 0
             int issued = 0;
             for (int li = 0; li < nst; ++li) {
                 const int it = kb + li;
@@ -434,6 +457,17 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 if (!ok) break;
                 issued = li + 1;
                 const int k0 = it * TK;
+                if (tiled) {
+                    // the whole box lands (rows past K belong to the next
+                    // problem or read as zero; the converters skip them)
+                    if (lane == 0) {
+                        mbar_expect_tx(full_r(r), (uint32_t)(TK * TN * 4));
+                        tensor_g2s_2d(smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES),
+                                      &g.bmap, cbase, y0 + k0, full_r(r));
+                    }
+                    __syncwarp();
+                    continue;
+                }
                 const int krows = max(0, min(TK, pr.K - k0));
                 if (lane == 0) mbar_expect_tx(full_r(r), rbytes * (uint32_t)krows);
                 __syncwarp();
@@ -1007,6 +1041,44 @@ void build_split_lists(int N, int Jh, int C, int tn, int plan, const std::vector
     }
 }
 
+// The driver's cuTensorMapEncodeTiled, reached through the runtime (no link
+// against libcuda); nullptr if the driver does not offer it.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+    static EncodeTiled fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiled) nullptr;
+        }
+        return reinterpret_cast<EncodeTiled>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of the forward operand B: rows x C floats, row pitch C (the
+// rows are 16-byte aligned), box tn columns x TK rows.  False if it cannot
+// be made (the row copies are used instead).
+bool encode_b_map(CUtensorMap* map, const void* B, int C, long long rows, int tn) {
+    const EncodeTiled enc = encode_tiled();
+    if (!enc || rows <= 0 || rows > (1LL << 31)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)C, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)C * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)tn, (cuuint32_t)TK};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(B), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* O) {
     const SplitTables* st = p->split;
     GemmArgs g;
@@ -1026,6 +1098,11 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.bplanes = inverse ? st->inv_bplanes : nullptr;
     g.stall = (!inverse && st->inject_stall) ? 1 : 0;
     g.bplane_bytes = inverse ? (long long)st->inv_bplane_bytes : 0;
+    // forward B: the Fourier workspace, problem (m, parity) at rows
+    // (2 m + parity) Jh .. + Jh - 1 of a [2 (N + 1) Jh][C] matrix
+    if (!inverse && g.raw_bulk &&
+        encode_b_map(&g.bmap, B, g.C, 2LL * (p->N + 1) * p->Jh, st->tn))
+        g.raw_bulk = 2;
     return g;
 }
 
