@@ -108,22 +108,30 @@ template <int TN> struct Wid {
     static constexpr int CTAS_PER_SM = TN == 64 ? 3 : 2;
 };
 
-// Stage layout: T A tiles | T 16-bit B tiles, in a ring of NS stages.  When
-// the GEMM converts B itself (not BPRE), the FP32 rows of B arrive in a
-// separate ring of NR slots (TK rows of TN each), filled by their own copy
-// warp and freed as soon as the converters have read them, so the long-
-// latency FP32 rows run further ahead than the A tiles.  Stage counts keep
+// Shared-memory rings.  Pre-split B (BPRE): NA slots of T A tiles followed
+// by T 16-bit B tiles, all loaded by the copy warp.  B converted in the
+// kernel: three rings, each as deep as its latency needs -- NA slots of T A
+// tiles (bulk copies from L2 / HBM, the longest wait), NR slots of FP32 B
+// rows (TK rows of TN, their own copy warp, freed as soon as the converters
+// have read them) and NB slots of the converted 16-bit B terms (written
+// just before the MMAs read them, so two or three suffice).  Counts keep
 // TN = 128 under 113 KB (two CTAs per SM, 2 x 256 TMEM columns) and TN = 64
 // under 75 KB (three CTAs per SM, 3 x 128 columns).
 template <int T, bool BPRE, int TN> struct Cfg {
-    static constexpr int NS = BPRE ? (T == 3 ? 4 : 6) : (T == 3 ? 3 : 4);
-    static constexpr int NR = BPRE ? 0 : (T == 3 ? 5 : 6);
-    static constexpr int BBF_OFF = T * A_TILE_BYTES;
-    static constexpr int STAGE_BYTES = BBF_OFF + T * Wid<TN>::B_TILE_BYTES;
-    static constexpr int RAW_OFF = NS * STAGE_BYTES;   // raw slot r at RAW_OFF + r RAW_BYTES
+    static constexpr int NA = BPRE ? (T == 3 ? 4 : 6)
+                                   : (TN == 128 ? (T == 3 ? 5 : 6) : (T == 3 ? 4 : 5));
+    static constexpr int NB = BPRE ? 0 : (TN == 128 && T == 2 ? 3 : 2);
+    static constexpr int NR = BPRE ? 0 : (T == 3 ? 3 : 4);
+    static constexpr int A_SLOT = T * A_TILE_BYTES + (BPRE ? T * Wid<TN>::B_TILE_BYTES : 0);
+    static constexpr int BPRE_OFF = T * A_TILE_BYTES;   // pre-split B tiles within an A slot
+    static constexpr int B_SLOT = T * Wid<TN>::B_TILE_BYTES;
+    static constexpr int B_OFF = NA * A_SLOT;           // B-term slot b at B_OFF + b B_SLOT
+    static constexpr int RAW_OFF = B_OFF + NB * B_SLOT;   // raw slot r at RAW_OFF + r RAW_BYTES
     static constexpr int BAR_OFF = RAW_OFF + NR * Wid<TN>::RAW_BYTES;
+    static constexpr int NBAR = 2 * NA + 2 * NB + 2 * NR + 1;
     static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
     static constexpr int SMEM = CSI_OFF + TN * 4;
+    static_assert(8 * NBAR + 12 <= 256, "barriers, TMEM address and abort flag fit 256 bytes");
 };
 static_assert(Cfg<3, false, 128>::SMEM <= 113 * 1024 && Cfg<2, false, 128>::SMEM <= 113 * 1024 &&
                   Cfg<3, true, 128>::SMEM <= 113 * 1024 && Cfg<2, true, 128>::SMEM <= 113 * 1024,
@@ -329,7 +337,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     using CF = Cfg<T, BPRE, TN>;
     constexpr int B_TILE_BYTES = Wid<TN>::B_TILE_BYTES;
     constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
-    constexpr int NS = CF::NS;
+    constexpr int NA = CF::NA;
+    constexpr int NBS = CF::NB;
     constexpr int NR = CF::NR;
     // With 128-wide column tiles the product is formed transposed,
     // D^T = B^T A^T, with the 128 columns of B on the MMA's M side and the
@@ -339,10 +348,11 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     // row as 32 adjacent columns per warp instruction (coalesced; with the
     // rows on the lanes, every lane would write its own row).
     constexpr bool SWAP = TN == 128;
-    constexpr int NB = 3 * NS + 2 * NR + 1;   // barriers
+    constexpr int NB = CF::NBAR;   // barriers
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
-    // bars: full_a[NS], full_b[NS], empty[NS], full_r[NR], empty_r[NR], done
+    // bars: full_a[NA], empty_a[NA], full_b[NBS], empty_b[NBS], full_r[NR],
+    // empty_r[NR], done
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * NB);
     volatile int* abort_flag =
         reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * NB + 8);
@@ -357,17 +367,21 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     const int nst = (mt < pr.mt0) ? 0 : pr.nkt - pr.kt0;
     const uint32_t bar0 = smem_u32(bars);
     auto full_a = [&](int s) { return bar0 + 8u * s; };
-    auto full_b = [&](int s) { return bar0 + 8u * (NS + s); };
-    auto empty = [&](int s) { return bar0 + 8u * (2 * NS + s); };
-    auto full_r = [&](int r) { return bar0 + 8u * (3 * NS + r); };
-    auto empty_r = [&](int r) { return bar0 + 8u * (3 * NS + NR + r); };
-    const uint32_t done = bar0 + 8u * (3 * NS + 2 * NR);
+    auto empty_a = [&](int s) { return bar0 + 8u * (NA + s); };
+    auto full_b = [&](int b) { return bar0 + 8u * (2 * NA + b); };
+    auto empty_b = [&](int b) { return bar0 + 8u * (2 * NA + NBS + b); };
+    auto full_r = [&](int r) { return bar0 + 8u * (2 * NA + 2 * NBS + r); };
+    auto empty_r = [&](int r) { return bar0 + 8u * (2 * NA + 2 * NBS + NR + r); };
+    const uint32_t done = bar0 + 8u * (2 * NA + 2 * NBS + 2 * NR);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NS; ++s) {
+        for (int s = 0; s < NA; ++s) {
             mbar_init(full_a(s), 1);
-            mbar_init(full_b(s), NCONV);
-            mbar_init(empty(s), 1);
+            mbar_init(empty_a(s), 1);
+        }
+        for (int b = 0; b < NBS; ++b) {
+            mbar_init(full_b(b), NCONV);
+            mbar_init(empty_b(b), 1);
         }
         for (int r = 0; r < NR; ++r) {
             mbar_init(full_r(r), 1);
@@ -397,15 +411,15 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         const bool stall = g.stall && blockIdx.x == 0;   // injected: stage 0 never armed
         for (int li = 0; li < nst; ++li) {
             const int it = kb + li;
-            const int s = li % NS;
-            const uint32_t ph = (uint32_t)(li / NS) & 1u;
+            const int s = li % NA;
+            const uint32_t ph = (uint32_t)(li / NA) & 1u;
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(empty(s), ph ^ 1u, abort_flag);
+            if (lane == 0) ok = mbar_wait(empty_a(s), ph ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             issued = li + 1;
             if (stall && li == 0) continue;
-            unsigned char* st = smem + s * CF::STAGE_BYTES;
+            unsigned char* st = smem + s * CF::A_SLOT;
             if (lane == 0) {
                 mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES) : 0u));
                 const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
@@ -418,7 +432,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                     const long long b_src =
                         pr.bt_off + ((long long)it * g.nct + ct) * B_TILE_BYTES;
                     for (int t = 0; t < T; ++t)
-                        bulk_g2s(smem_u32(st + CF::BBF_OFF + t * B_TILE_BYTES),
+                        bulk_g2s(smem_u32(st + CF::BPRE_OFF + t * B_TILE_BYTES),
                                  g.bplanes + (long long)t * g.bplane_bytes + b_src,
                                  B_TILE_BYTES, full_a(s));
                 }
@@ -428,10 +442,10 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         // after an abort, let the copies already issued land before the CTA
         // releases its shared memory (bounded; a stage never armed is skipped)
         if (lane == 0 && *abort_flag) {
-            for (int j = max(0, issued - NS); j < issued; ++j) {
+            for (int j = max(0, issued - NA); j < issued; ++j) {
                 if (stall && j == 0) continue;
                 const long long t0 = clock64();
-                while (!mbar_try(full_a(j % NS), (uint32_t)(j / NS) & 1u) &&
+                while (!mbar_try(full_a(j % NA), (uint32_t)(j / NA) & 1u) &&
                        clock64() - t0 < kWaitCycles) {
                 }
             }
@@ -500,14 +514,16 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             (void)idesc_swap;
             bool ok = true;
             for (int li = 0; li < nst && ok; ++li) {
-                const int s = li % NS;
-                const uint32_t ph = (uint32_t)(li / NS) & 1u;
-                ok = mbar_wait(full_a(s), ph, abort_flag) &&
-                     (BPRE || mbar_wait(full_b(s), ph, abort_flag));
+                const int s = li % NA;
+                constexpr int NBB = NBS > 0 ? NBS : 1;
+                const int sb = li % NBB;
+                ok = mbar_wait(full_a(s), (uint32_t)(li / NA) & 1u, abort_flag) &&
+                     (BPRE || mbar_wait(full_b(sb), (uint32_t)(li / NBB) & 1u, abort_flag));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = smem_u32(smem + s * CF::STAGE_BYTES);
-                const uint32_t bst = st + CF::BBF_OFF;
+                const uint32_t st = smem_u32(smem + s * CF::A_SLOT);
+                const uint32_t bst = BPRE ? st + CF::BPRE_OFF
+                                          : smem_u32(smem + CF::B_OFF + sb * CF::B_SLOT);
 #pragma unroll
                 for (int ks = 0; ks < TK / UK; ++ks) {
 #pragma unroll
@@ -531,7 +547,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                         }
                     }
                 }
-                mma_commit(empty(s));
+                mma_commit(empty_a(s));
+                if (!BPRE) mma_commit(empty_b(sb));
             }
             // done fires once every MMA issued so far has completed
             mma_commit(done);
@@ -555,16 +572,15 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
         constexpr int NRS = NR > 0 ? NR : 1;
         for (int li = 0; li < (BPRE ? 0 : nst); ++li) {
             const int it = kb + li;
-            const int s = li % NS, r = li % NRS;
-            const uint32_t ph = (uint32_t)(li / NS) & 1u;
-            // the stage's B-term area is free once the MMAs of its previous
-            // use are done; the FP32 rows wait in raw slot r
-            if (!mbar_wait(empty(s), ph ^ 1u, abort_flag)) break;
+            constexpr int NBB = NBS > 0 ? NBS : 1;
+            const int sb = li % NBB, r = li % NRS;
+            // B-term slot sb is free once the MMAs of its previous use are
+            // done; the FP32 rows wait in raw slot r
+            if (!mbar_wait(empty_b(sb), ((uint32_t)(li / NBB) & 1u) ^ 1u, abort_flag)) break;
             if (g.raw_bulk && !mbar_wait(full_r(r), (uint32_t)(li / NRS) & 1u, abort_flag)) break;
-            unsigned char* stg = smem + s * CF::STAGE_BYTES;
             const float* raw =
                 reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
-            unsigned char* bst = stg + CF::BBF_OFF;
+            unsigned char* bst = smem + CF::B_OFF + sb * CF::B_SLOT;
             const int k0 = it * TK;
 #pragma unroll
             for (int u = tid; u < TN * TK / 8; u += NCONV) {
@@ -599,7 +615,7 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(full_b(s));
+            mbar_arrive(full_b(sb));
             if (g.raw_bulk) mbar_arrive(empty_r(r));
         }
         // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the tile

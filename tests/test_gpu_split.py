@@ -66,6 +66,10 @@ CASES = [
     (40, 81, 96, 2),
     (63, 129, 256, 19),
     (159, 321, 640, 33),
+    # 3 and 4 column tiles: clusters of 3 and 4 CTAs share each P~ tile
+    # (at T31 a row tile has at most 2 groups of 8 rows, fewer than CTAs)
+    (63, 129, 256, 160),
+    (31, 65, 128, 256),
 ]
 
 
