@@ -43,6 +43,8 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "sht_internal.h"
@@ -128,9 +130,8 @@ template <int T, bool BPRE, int TN> struct Cfg {
     static constexpr int B_OFF = NA * A_SLOT;           // B-term slot b at B_OFF + b B_SLOT
     static constexpr int RAW_OFF = B_OFF + NB * B_SLOT;   // raw slot r at RAW_OFF + r RAW_BYTES
     static constexpr int BAR_OFF = RAW_OFF + NR * Wid<TN>::RAW_BYTES;
-    static constexpr int NBAR = 2 * NA + 2 * NB + 2 * NR + 1;
-    static constexpr int CSI_OFF = BAR_OFF + 256;   // FP16: TN column unscale factors
-    static constexpr int SMEM = CSI_OFF + TN * 4;
+    static constexpr int NBAR = 2 * NA + 2 * NB + 2 * NR + 3;
+    static constexpr int SMEM = BAR_OFF + 256;
     static_assert(8 * NBAR + 12 <= 256, "barriers, TMEM address and abort flag fit 256 bytes");
 };
 static_assert(Cfg<3, false, 128>::SMEM <= 113 * 1024 && Cfg<2, false, 128>::SMEM <= 113 * 1024 &&
@@ -145,6 +146,7 @@ struct GemmArgs {
     long long plane_bytes;
     const SplitProb* probs;
     const int4* tiles;
+    int ntiles;                     // tiles in the list (persistent CTAs stride over them)
     const float* B;
     float* O;
     int C;                          // valid columns (2F)
@@ -332,14 +334,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 extern __shared__ __align__(1024) unsigned char split_smem[];
 
-template <int T, bool F16, bool BPRE, int TN>
-__device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 tile) {
+// Per-tile arguments of a launch: one plan's for every tile, or, for a
+// grouped launch, those of plan tile.w.
+struct OnePlanArgs {
+    const GemmArgs& g;
+    __device__ __forceinline__ const GemmArgs& operator()(const int4&) const { return g; }
+    __device__ __forceinline__ void mark_timeout() const {
+        if (g.status) atomicOr(g.status, 1);
+    }
+};
+struct GroupPlanArgs {
+    const GemmArgs* a;
+    int n;
+    __device__ __forceinline__ const GemmArgs& operator()(const int4& t) const { return a[t.w]; }
+    __device__ __forceinline__ void mark_timeout() const {
+        for (int q = 0; q < n; ++q)
+            if (a[q].status) atomicOr(a[q].status, 1);
+    }
+};
+
+// Persistent CTAs: CTA b computes tiles b, b + gridDim.x, ... of the list.
+// The rings and their phases run on across tiles (every role walks the
+// same tiles and stages, so its running stage count names the slot and
+// phase), the copy warps prefetch the next tile's operands while the
+// converter warps drain the accumulator of the last one, and the MMA warp
+// starts a tile once that drain is done (acc_empty).
+template <int T, bool F16, bool BPRE, int TN, class Args>
+__device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __restrict__ tiles,
+                                                int ntiles) {
     using CF = Cfg<T, BPRE, TN>;
     constexpr int B_TILE_BYTES = Wid<TN>::B_TILE_BYTES;
     constexpr int TMEM_COLS = Wid<TN>::TMEM_COLS;
     constexpr int NA = CF::NA;
     constexpr int NBS = CF::NB;
     constexpr int NR = CF::NR;
+    constexpr int NBB = NBS > 0 ? NBS : 1;
+    constexpr int NRS = NR > 0 ? NR : 1;
     // With 128-wide column tiles the product is formed transposed,
     // D^T = B^T A^T, with the 128 columns of B on the MMA's M side and the
     // tile's A rows (at most 128, rounded up to 16) on its N side, so a
@@ -352,19 +382,12 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     unsigned char* smem = split_smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + CF::BAR_OFF);
     // bars: full_a[NA], empty_a[NA], full_b[NBS], empty_b[NBS], full_r[NR],
-    // empty_r[NR], done
+    // empty_r[NR], done, acc_empty, fin
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + CF::BAR_OFF + 8 * NB);
     volatile int* abort_flag =
         reinterpret_cast<volatile int*>(smem + CF::BAR_OFF + 8 * NB + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const SplitProb pr = g.probs[tile.x];
-    const int mt = tile.y, ct = tile.z;
-    // stages it = kb .. kb + nst - 1 (the reduced transform skips the K tiles
-    // of negligible P~ in the forward direction and whole row tiles in the
-    // inverse one, whose outputs are then written as zero)
-    const int kb = pr.kt0;
-    const int nst = (mt < pr.mt0) ? 0 : pr.nkt - pr.kt0;
     const uint32_t bar0 = smem_u32(bars);
     auto full_a = [&](int s) { return bar0 + 8u * s; };
     auto empty_a = [&](int s) { return bar0 + 8u * (NA + s); };
@@ -372,7 +395,9 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     auto empty_b = [&](int b) { return bar0 + 8u * (2 * NA + NBS + b); };
     auto full_r = [&](int r) { return bar0 + 8u * (2 * NA + 2 * NBS + r); };
     auto empty_r = [&](int r) { return bar0 + 8u * (2 * NA + 2 * NBS + NR + r); };
-    const uint32_t done = bar0 + 8u * (2 * NA + 2 * NBS + 2 * NR);
+    const uint32_t done = bar0 + 8u * (2 * NA + 2 * NBS + 2 * NR);   // accumulator full
+    const uint32_t acc_empty = done + 8u;   // accumulator read out by the epilogue
+    const uint32_t fin = done + 16u;        // every MMA of the CTA completed
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) {
@@ -388,6 +413,8 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
             mbar_init(empty_r(r), NCONV);
         }
         mbar_init(done, 1);
+        mbar_init(acc_empty, NCONV);
+        mbar_init(fin, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -403,81 +430,103 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
+    // stages it = kb .. kb + nst - 1 of a tile (the reduced transform skips
+    // the K tiles of negligible P~ in the forward direction and whole row
+    // tiles in the inverse one, whose outputs are then written as zero)
+    auto stages = [](const SplitProb& pr, int mt) { return (mt < pr.mt0) ? 0 : pr.nkt - pr.kt0; };
+    // warp-uniform view of the abort flag
+    auto aborted = [&]() { return __any_sync(0xffffffffu, *abort_flag != 0) != 0; };
+
     if (warp == WARP_PRODUCER) {
         // ---- producer: A tiles (and pre-split B tiles), lane 0 ----
-        const uint32_t abytes = (uint32_t)h * TK * 2;
-        int issued = 0;
-        const bool stall = g.stall && blockIdx.x == 0;   // injected: stage 0 never armed
-        for (int li = 0; li < nst; ++li) {
-            const int it = kb + li;
-            const int s = li % NA;
-            const uint32_t ph = (uint32_t)(li / NA) & 1u;
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(empty_a(s), ph ^ 1u, abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) break;
-            issued = li + 1;
-            if (stall && li == 0) continue;
-            unsigned char* st = smem + s * CF::A_SLOT;
-            if (lane == 0) {
-                mbar_expect_tx(full_a(s), abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES) : 0u));
-                const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
-                                          (long long)mt * TM * TK * 2;
-                for (int t = 0; t < T; ++t)
-                    bulk_g2s(smem_u32(st + t * A_TILE_BYTES),
-                             g.planes + (long long)t * g.plane_bytes + src_off, abytes,
-                             full_a(s));
-                if (BPRE) {
-                    const long long b_src =
-                        pr.bt_off + ((long long)it * g.nct + ct) * B_TILE_BYTES;
-                    for (int t = 0; t < T; ++t)
-                        bulk_g2s(smem_u32(st + CF::BPRE_OFF + t * B_TILE_BYTES),
-                                 g.bplanes + (long long)t * g.bplane_bytes + b_src,
-                                 B_TILE_BYTES, full_a(s));
+        uint32_t q = 0, issued = 0;   // stages passed / issued in this CTA
+        bool stalled = false;         // injected: the CTA's first stage never armed
+        bool ok = true;
+        for (int tt = blockIdx.x; tt < ntiles && ok && !aborted(); tt += gridDim.x) {
+            const int4 tile = tiles[tt];
+            const GemmArgs& g = args(tile);
+            const SplitProb pr = g.probs[tile.x];
+            const int mt = tile.y, ct = tile.z, kb = pr.kt0, nst = stages(pr, mt);
+            const int h = min(TM, pr.R8 - TM * mt);   // A rows present in this tile
+            const uint32_t abytes = (uint32_t)h * TK * 2;
+            for (int li = 0; li < nst; ++li, ++q) {
+                const int it = kb + li;
+                const int s = q % NA;
+                const uint32_t ph = (q / NA) & 1u;
+                if (lane == 0) ok = mbar_wait(empty_a(s), ph ^ 1u, abort_flag);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) break;
+                issued = q + 1;
+                if (q == 0 && g.stall && blockIdx.x == 0) {
+                    stalled = true;
+                    continue;
                 }
+                unsigned char* st = smem + s * CF::A_SLOT;
+                if (lane == 0) {
+                    mbar_expect_tx(full_a(s),
+                                   abytes * T + (BPRE ? (uint32_t)(T * B_TILE_BYTES) : 0u));
+                    const long long src_off = pr.a_off + (long long)it * pr.R8 * TK * 2 +
+                                              (long long)mt * TM * TK * 2;
+                    for (int t = 0; t < T; ++t)
+                        bulk_g2s(smem_u32(st + t * A_TILE_BYTES),
+                                 g.planes + (long long)t * g.plane_bytes + src_off, abytes,
+                                 full_a(s));
+                    if (BPRE) {
+                        const long long b_src =
+                            pr.bt_off + ((long long)it * g.nct + ct) * B_TILE_BYTES;
+                        for (int t = 0; t < T; ++t)
+                            bulk_g2s(smem_u32(st + CF::BPRE_OFF + t * B_TILE_BYTES),
+                                     g.bplanes + (long long)t * g.bplane_bytes + b_src,
+                                     B_TILE_BYTES, full_a(s));
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
         }
         // after an abort, let the copies already issued land before the CTA
         // releases its shared memory (bounded; a stage never armed is skipped)
         if (lane == 0 && *abort_flag) {
-            for (int j = max(0, issued - NA); j < issued; ++j) {
-                if (stall && j == 0) continue;
+            for (uint32_t j = issued > (uint32_t)NA ? issued - NA : 0u; j < issued; ++j) {
+                if (stalled && j == 0) continue;
                 const long long t0 = clock64();
-                while (!mbar_try(full_a(j % NA), (uint32_t)(j / NA) & 1u) &&
+                while (!mbar_try(full_a(j % NA), (j / NA) & 1u) &&
                        clock64() - t0 < kWaitCycles) {
                 }
             }
         }
     } else if (warp == WARP_RAW) {
-        // ---- the FP32 rows of B (lane k copies row k of a stage) into the
-        // raw ring, NR stages ahead of the converters ----
-        if (!BPRE && g.raw_bulk) {
+        // ---- the FP32 rows of B into the raw ring, NR stages ahead of the
+        // converters: one tiled tensor copy per stage, or one bulk copy per
+        // row (lane k copies row k) ----
+        uint32_t q = 0, issued = 0;   // raw stages passed / issued in this CTA
+        bool ok = true;
+        for (int tt = blockIdx.x; !BPRE && tt < ntiles && ok && !aborted(); tt += gridDim.x) {
+            const int4 tile = tiles[tt];
+            const GemmArgs& g = args(tile);
+            if (!g.raw_bulk) continue;
+            const SplitProb pr = g.probs[tile.x];
+            const int mt = tile.y, ct = tile.z, kb = pr.kt0, nst = stages(pr, mt);
             const int cbase = ct * TN;
             const int ccopy = min(TN, g.C - cbase);   // valid columns
             const uint32_t rbytes = (uint32_t)ccopy * 4u;
-            constexpr int NRS = NR > 0 ? NR : 1;
             const bool tiled = g.raw_bulk == 2;
             const int y0 = tiled ? (int)(pr.b_off / pr.b_stride) : 0;   // matrix row of k = 0
-            int issued = 0;
-            for (int li = 0; li < nst; ++li) {
+            for (int li = 0; li < nst; ++li, ++q) {
                 const int it = kb + li;
-                const int r = li % NRS;
-                const uint32_t ph = (uint32_t)(li / NRS) & 1u;
-                bool ok = true;
+                const int r = q % NRS;
+                const uint32_t ph = (q / NRS) & 1u;
                 if (lane == 0) ok = mbar_wait(empty_r(r), ph ^ 1u, abort_flag);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
-                issued = li + 1;
+                issued = q + 1;
                 const int k0 = it * TK;
+                const uint32_t dst = smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
                 if (tiled) {
                     // the whole box lands (rows past K belong to the next
                     // problem or read as zero; the converters skip them)
                     if (lane == 0) {
                         mbar_expect_tx(full_r(r), (uint32_t)(TK * TN * 4));
-                        tensor_g2s_2d(smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES),
-                                      &g.bmap, cbase, y0 + k0, full_r(r));
+                        tensor_g2s_2d(dst, &g.bmap, cbase, y0 + k0, full_r(r));
                     }
                     __syncwarp();
                     continue;
@@ -485,256 +534,294 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
                 const int krows = max(0, min(TK, pr.K - k0));
                 if (lane == 0) mbar_expect_tx(full_r(r), rbytes * (uint32_t)krows);
                 __syncwarp();
-                if (lane < krows) {
-                    const float* src =
-                        g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase;
-                    bulk_g2s(smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES + lane * TN * 4),
-                             src, rbytes, full_r(r));
-                }
+                if (lane < krows)
+                    bulk_g2s(dst + lane * TN * 4,
+                             g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase,
+                             rbytes, full_r(r));
                 __syncwarp();
             }
-            // after an abort, let the row copies already issued land (bounded)
-            if (lane == 0 && *abort_flag) {
-                for (int j = max(0, issued - NRS); j < issued; ++j) {
-                    const long long t0 = clock64();
-                    while (!mbar_try(full_r(j % NRS), (uint32_t)(j / NRS) & 1u) &&
-                           clock64() - t0 < kWaitCycles) {
-                    }
+        }
+        // after an abort, let the row copies already issued land (bounded)
+        if (lane == 0 && *abort_flag) {
+            for (uint32_t j = issued > (uint32_t)NRS ? issued - NRS : 0u; j < issued; ++j) {
+                const long long t0 = clock64();
+                while (!mbar_try(full_r(j % NRS), (j / NRS) & 1u) &&
+                       clock64() - t0 < kWaitCycles) {
                 }
             }
         }
     } else if (warp == WARP_MMA) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            // SWAP: M = 128 (the column tile), N = the tile's A rows rounded to 16
-            const int nrows = ((min(TM, pr.R8 - TM * mt) + 15) / 16) * 16;
-            const uint32_t idesc_swap = (1u << 4) | (F16 ? 0u : ((1u << 7) | (1u << 10))) |
-                                        ((uint32_t)(nrows >> 3) << 17) |
-                                        ((uint32_t)(TM >> 4) << 24);
-            (void)idesc_swap;
+            uint32_t q = 0, qb = 0;   // stages of the A ring / B-term ring passed
+            uint32_t nacc = 0;        // tiles accumulated so far
             bool ok = true;
-            for (int li = 0; li < nst && ok; ++li) {
-                const int s = li % NA;
-                constexpr int NBB = NBS > 0 ? NBS : 1;
-                const int sb = li % NBB;
-                ok = mbar_wait(full_a(s), (uint32_t)(li / NA) & 1u, abort_flag) &&
-                     (BPRE || mbar_wait(full_b(sb), (uint32_t)(li / NBB) & 1u, abort_flag));
-                if (!ok) break;
+            for (int tt = blockIdx.x; tt < ntiles && ok && !*abort_flag; tt += gridDim.x) {
+                const int4 tile = tiles[tt];
+                const SplitProb pr = args(tile).probs[tile.x];
+                const int mt = tile.y, nst = stages(pr, mt);
+                if (nst == 0) continue;
+                // SWAP: M = 128 (the column tile), N = the tile's A rows rounded to 16
+                const int nrows = ((min(TM, pr.R8 - TM * mt) + 15) / 16) * 16;
+                const uint32_t idesc_swap = (1u << 4) | (F16 ? 0u : ((1u << 7) | (1u << 10))) |
+                                            ((uint32_t)(nrows >> 3) << 17) |
+                                            ((uint32_t)(TM >> 4) << 24);
+                (void)idesc_swap;
+                // the epilogue has read the previous tile's accumulator
+                if (nacc > 0 && !(ok = mbar_wait(acc_empty, (nacc - 1) & 1u, abort_flag))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = smem_u32(smem + s * CF::A_SLOT);
-                const uint32_t bst = BPRE ? st + CF::BPRE_OFF
-                                          : smem_u32(smem + CF::B_OFF + sb * CF::B_SLOT);
+                for (int li = 0; li < nst; ++li, ++q) {
+                    const int s = q % NA;
+                    const int sb = qb % NBB;
+                    ok = mbar_wait(full_a(s), (q / NA) & 1u, abort_flag) &&
+                         (BPRE || mbar_wait(full_b(sb), (qb / NBB) & 1u, abort_flag));
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = smem_u32(smem + s * CF::A_SLOT);
+                    const uint32_t bst = BPRE ? st + CF::BPRE_OFF
+                                              : smem_u32(smem + CF::B_OFF + sb * CF::B_SLOT);
 #pragma unroll
-                for (int ks = 0; ks < TK / UK; ++ks) {
+                    for (int ks = 0; ks < TK / UK; ++ks) {
 #pragma unroll
-                    for (int a = 0; a < T; ++a) {
+                        for (int a = 0; a < T; ++a) {
 #pragma unroll
-                        for (int b = 0; b < T - a; ++b) {
-                            // FP16: x_2 y_2 has weight 2^-22 (below 2^-24 of
-                            // the scaled operands) and is dropped
-                            if (F16 && a == 1 && b == 1) continue;
-                            const uint64_t ad = sdesc(st + a * A_TILE_BYTES + ks * 256, 128, kSBO);
-                            const uint64_t bd = sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, kSBO);
-                            // (0,0) -> leading accumulator; the first of the
-                            // others, (0,1), opens the correction accumulator
-                            const bool lead = (a == 0 && b == 0);
-                            const uint32_t acc =
-                                (li > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u : 0u;
-                            if constexpr (SWAP)
-                                mma_f16_rt(lead ? tmem : tmem + TN, bd, ad, idesc_swap, acc);
-                            else
-                                mma_f16<F16, TN>(lead ? tmem : tmem + TN, ad, bd, acc);
+                            for (int b = 0; b < T - a; ++b) {
+                                // FP16: x_2 y_2 has weight 2^-22 (below 2^-24
+                                // of the scaled operands) and is dropped
+                                if (F16 && a == 1 && b == 1) continue;
+                                const uint64_t ad =
+                                    sdesc(st + a * A_TILE_BYTES + ks * 256, 128, kSBO);
+                                const uint64_t bd =
+                                    sdesc(bst + b * B_TILE_BYTES + ks * 256, 128, kSBO);
+                                // (0,0) -> leading accumulator; the first of
+                                // the others, (0,1), opens the correction one
+                                const bool lead = (a == 0 && b == 0);
+                                const uint32_t acc =
+                                    (li > 0 || ks > 0 || !(lead || (a == 0 && b == 1))) ? 1u
+                                                                                         : 0u;
+                                if constexpr (SWAP)
+                                    mma_f16_rt(lead ? tmem : tmem + TN, bd, ad, idesc_swap, acc);
+                                else
+                                    mma_f16<F16, TN>(lead ? tmem : tmem + TN, ad, bd, acc);
+                            }
                         }
                     }
+                    mma_commit(empty_a(s));
+                    if (!BPRE) {
+                        mma_commit(empty_b(sb));
+                        ++qb;
+                    }
                 }
-                mma_commit(empty_a(s));
-                if (!BPRE) mma_commit(empty_b(sb));
+                if (!ok) break;
+                // done fires once every MMA of the tile has completed
+                mma_commit(done);
+                ++nacc;
             }
-            // done fires once every MMA issued so far has completed
-            mma_commit(done);
+            // fin fires once every MMA this CTA issued has completed
+            mma_commit(fin);
         }
     } else {
-        // ---- converters: B (FP32, rows k, columns c) -> T BF16 K-major tiles ----
+        // ---- converters: B (FP32, rows k, columns c) -> T BF16 K-major tiles
         // from the staged rows in shared memory (raw_bulk) or straight from
-        // global memory (rows not 16-byte aligned: odd field counts)
+        // global memory (rows not 16-byte aligned: odd field counts); then
+        // the tile's epilogue ----
         const int tid = threadIdx.x;   // 0..NCONV-1
-        const int cbase = ct * TN;
         static_assert(NCONV % TN == 0, "a converter thread keeps one column");
-        float cs = 1.f;
-        float* csi_s = reinterpret_cast<float*>(smem + CF::CSI_OFF);
-        if (F16) {
-            const int cg = cbase + tid % TN;
-            if (cg < g.C) cs = col_scale(g.colmax[cg]);
-            if (tid < TN) csi_s[tid] = cg < g.C ? col_unscale(g.colmax[cg]) : 0.f;
-            // the epilogue of all converter warps reads the table
-            asm volatile("bar.sync 1, %0;" ::"r"(NCONV) : "memory");
-        }
-        constexpr int NRS = NR > 0 ? NR : 1;
-        for (int li = 0; li < (BPRE ? 0 : nst); ++li) {
-            const int it = kb + li;
-            constexpr int NBB = NBS > 0 ? NBS : 1;
-            const int sb = li % NBB, r = li % NRS;
-            // B-term slot sb is free once the MMAs of its previous use are
-            // done; the FP32 rows wait in raw slot r
-            if (!mbar_wait(empty_b(sb), ((uint32_t)(li / NBB) & 1u) ^ 1u, abort_flag)) break;
-            if (g.raw_bulk && !mbar_wait(full_r(r), (uint32_t)(li / NRS) & 1u, abort_flag)) break;
-            const float* raw =
-                reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
-            unsigned char* bst = smem + CF::B_OFF + sb * CF::B_SLOT;
-            const int k0 = it * TK;
-#pragma unroll
-            for (int u = tid; u < TN * TK / 8; u += NCONV) {
-                const int c = u % TN;
-                const int k8 = u / TN;
-                const int cg = cbase + c;
-                float x[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int kk = k8 * 8 + e;
-                    const bool in = (k0 + kk < pr.K) && (cg < g.C);
-                    if (g.raw_bulk)
-                        x[e] = in ? raw[kk * TN + c] : 0.f;
-                    else
-                        x[e] = in ? __ldg(g.B + pr.b_off + (long long)(k0 + kk) * pr.b_stride + cg)
-                                  : 0.f;
-                }
-                const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
-                if (F16) {
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] *= cs;
-                }
-#pragma unroll
-                for (int t = 0; t < T; ++t) {
-                    const uint4 pk = t == T - 1 ? split_term8<F16, true>(x)
-                                                : split_term8<F16, false>(x);
-                    if (F16 && t == 0) {
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) x[e] *= 2048.f;   // x_2, x_3: weight 2^-11
-                    }
-                    *reinterpret_cast<uint4*>(bst + t * B_TILE_BYTES + off) = pk;
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(full_b(sb));
-            if (g.raw_bulk) mbar_arrive(empty_r(r));
-        }
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the tile
-        // rows it may access) for column half w / 4 ----
-        const bool have = nst > 0;
+        uint32_t qb = 0, qr = 0;   // B-term / raw ring stages passed
+        uint32_t nacc = 0;         // tiles accumulated so far
         bool ok = true;
-        if (have) ok = mbar_wait(done, 0, abort_flag);
-        // the TMEM loads and shuffles below are warp-collective: agree on ok
-        ok = __all_sync(0xffffffffu, ok) != 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int lq = warp & 3, half = warp >> 2;
-        if constexpr (SWAP) {
-            // TMEM lane 32 lq + lane = column c of the tile; TMEM columns =
-            // rows n.  For each row the 32 lanes store 32 adjacent columns.
-            const int c = cbase + 32 * lq + lane;
-            const bool col_ok = c < g.C && ok && !*abort_flag;
-            const float csi = (F16 && c < g.C) ? col_unscale(g.colmax[c]) : 0.f;
-            constexpr int NCH = TN / 16 / (NCONV / 128);
-            for (int cc = 0; cc < NCH; ++cc) {
-                const int ch = half * NCH + cc;
-                const int n0 = TM * mt + ch * 16;
-                if (n0 >= pr.Mrows) break;   // uniform over the warp
-                uint32_t r[16];
-                if (have && ok) {
-                    uint32_t r2[16];
-                    const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
-                    tmem_ld16(ta, r);
-                    tmem_ld16(ta + TN, r2);
-                    // FP16: lane k < 16 fetches the row scale of row n0 + k
-                    const int nl = n0 + (lane & 15);
-                    const float my_rsi =
-                        (F16 && nl < pr.Mrows) ? g.rs_inv[pr.rs_off + nl] : 0.f;
+        for (int tt = blockIdx.x; tt < ntiles && ok && !aborted(); tt += gridDim.x) {
+            const int4 tile = tiles[tt];
+            const GemmArgs& g = args(tile);
+            const SplitProb pr = g.probs[tile.x];
+            const int mt = tile.y, ct = tile.z, kb = pr.kt0, nst = stages(pr, mt);
+            const int cbase = ct * TN;
+            float cs = 1.f;
+            if (F16) {
+                const int cg = cbase + tid % TN;
+                if (cg < g.C) cs = col_scale(g.colmax[cg]);
+            }
+            for (int li = 0; li < (BPRE ? 0 : nst); ++li, ++qb) {
+                const int it = kb + li;
+                const int sb = qb % NBB, r = qr % NRS;
+                // B-term slot sb is free once the MMAs of its previous use
+                // are done; the FP32 rows wait in raw slot r
+                // (a lane that gives up leaves alone; the warp agrees on ok
+                // again before the epilogue's collective operations)
+                if (!(ok = mbar_wait(empty_b(sb), ((qb / NBB) & 1u) ^ 1u, abort_flag))) break;
+                if (g.raw_bulk && !(ok = mbar_wait(full_r(r), (qr / NRS) & 1u, abort_flag)))
+                    break;
+                const float* raw =
+                    reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
+                unsigned char* bst = smem + CF::B_OFF + sb * CF::B_SLOT;
+                const int k0 = it * TK;
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        float v;
-                        if (F16) {
-                            const float rsi = __shfl_sync(0xffffffffu, my_rsi, k);
-                            v = (__uint_as_float(r[k]) + __uint_as_float(r2[k]) * (1.f / 2048.f)) *
-                                rsi * csi;
-                        } else {
-                            v = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
+                for (int u = tid; u < TN * TK / 8; u += NCONV) {
+                    const int c = u % TN;
+                    const int k8 = u / TN;
+                    const int cg = cbase + c;
+                    float x[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int kk = k8 * 8 + e;
+                        const bool in = (k0 + kk < pr.K) && (cg < g.C);
+                        if (g.raw_bulk)
+                            x[e] = in ? raw[kk * TN + c] : 0.f;
+                        else
+                            x[e] = in ? __ldg(g.B + pr.b_off + (long long)(k0 + kk) * pr.b_stride +
+                                              cg)
+                                      : 0.f;
+                    }
+                    const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
+                    if (F16) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] *= cs;
+                    }
+#pragma unroll
+                    for (int t = 0; t < T; ++t) {
+                        const uint4 pk = t == T - 1 ? split_term8<F16, true>(x)
+                                                    : split_term8<F16, false>(x);
+                        if (F16 && t == 0) {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) x[e] *= 2048.f;   // x_2, x_3: weight 2^-11
                         }
-                        r[k] = __float_as_uint(v);
+                        *reinterpret_cast<uint4*>(bst + t * B_TILE_BYTES + off) = pk;
                     }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) r[k] = 0u;
                 }
-                if (!col_ok) continue;
-                float* ocol = g.O + pr.o_off + c;
-#pragma unroll
-                for (int k = 0; k < 16; ++k)
-                    if (n0 + k < pr.Mrows)
-                        ocol[(long long)(n0 + k) * pr.o_stride] = __uint_as_float(r[k]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(full_b(sb));
+                if (g.raw_bulk) {
+                    mbar_arrive(empty_r(r));
+                    ++qr;
+                }
             }
-        } else {
-        const int row = TM * mt + 32 * lq + lane;
-        const bool row_ok = row < pr.Mrows && ok && !*abort_flag;
-        float* orow = g.O + pr.o_off + (long long)row * pr.o_stride;
-        const bool vec = ((pr.o_stride & 3) == 0) && ((pr.o_off & 3) == 0) &&
-                         ((g.C & 3) == 0);
-        constexpr int NCH = TN / 16 / (NCONV / 128);
-        for (int cc = 0; cc < NCH; ++cc) {
-            const int ch = half * NCH + cc;
-            uint32_t r[16];
+            // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the
+            // tile rows it may access) for column half w / 4 ----
+            const bool have = nst > 0;
+            if (have && ok) ok = mbar_wait(done, nacc & 1u, abort_flag);
+            // the TMEM loads and shuffles below are warp-collective: agree on ok
+            ok = __all_sync(0xffffffffu, ok) != 0;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int lq = warp & 3, half = warp >> 2;
+            if constexpr (SWAP) {
+                // TMEM lane 32 lq + lane = column c of the tile; TMEM columns =
+                // rows n.  For each row the 32 lanes store 32 adjacent columns.
+                const int c = cbase + 32 * lq + lane;
+                const bool col_ok = c < g.C && ok && !*abort_flag;
+                const float csi = (F16 && c < g.C) ? col_unscale(g.colmax[c]) : 0.f;
+                constexpr int NCH = TN / 16 / (NCONV / 128);
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int ch = half * NCH + cc;
+                    const int n0 = TM * mt + ch * 16;
+                    if (n0 >= pr.Mrows) break;   // uniform over the warp
+                    uint32_t r[16];
+                    if (have && ok) {
+                        uint32_t r2[16];
+                        const uint32_t ta =
+                            tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
+                        tmem_ld16(ta, r);
+                        tmem_ld16(ta + TN, r2);
+                        // FP16: lane k < 16 fetches the row scale of row n0 + k
+                        const int nl = n0 + (lane & 15);
+                        const float my_rsi =
+                            (F16 && nl < pr.Mrows) ? g.rs_inv[pr.rs_off + nl] : 0.f;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            float v;
+                            if (F16) {
+                                const float rsi = __shfl_sync(0xffffffffu, my_rsi, k);
+                                v = (__uint_as_float(r[k]) +
+                                     __uint_as_float(r2[k]) * (1.f / 2048.f)) *
+                                    rsi * csi;
+                            } else {
+                                v = __uint_as_float(r[k]) + __uint_as_float(r2[k]);
+                            }
+                            r[k] = __float_as_uint(v);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) r[k] = 0u;
+                    }
+                    if (!col_ok) continue;
+                    float* ocol = g.O + pr.o_off + c;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (n0 + k < pr.Mrows)
+                            ocol[(long long)(n0 + k) * pr.o_stride] = __uint_as_float(r[k]);
+                }
+            } else {
+                const int row = TM * mt + 32 * lq + lane;
+                const bool row_ok = row < pr.Mrows && ok && !*abort_flag;
+                float* orow = g.O + pr.o_off + (long long)row * pr.o_stride;
+                const bool vec = ((pr.o_stride & 3) == 0) && ((pr.o_off & 3) == 0) &&
+                                 ((g.C & 3) == 0);
+                constexpr int NCH = TN / 16 / (NCONV / 128);
+                for (int cc = 0; cc < NCH; ++cc) {
+                    const int ch = half * NCH + cc;
+                    const int c0 = cbase + ch * 16;
+                    uint32_t r[16];
+                    if (have && ok) {
+                        uint32_t r2[16];
+                        const uint32_t ta =
+                            tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
+                        tmem_ld16(ta, r);
+                        tmem_ld16(ta + TN, r2);
+                        if (F16) {
+                            // lead + 2^-11 corrections, then undo the row and
+                            // column scales
+                            const float rsi = row_ok ? g.rs_inv[pr.rs_off + row] : 0.f;
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const float csi =
+                                    c0 + i < g.C ? col_unscale(g.colmax[c0 + i]) : 0.f;
+                                r[i] = __float_as_uint((__uint_as_float(r[i]) +
+                                                        __uint_as_float(r2[i]) * (1.f / 2048.f)) *
+                                                       rsi * csi);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                r[i] = __float_as_uint(__uint_as_float(r[i]) +
+                                                       __uint_as_float(r2[i]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) r[i] = 0u;
+                    }
+                    if (!row_ok || c0 >= g.C) continue;
+                    if (vec && c0 + 16 <= g.C) {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float4 f;
+                            f.x = __uint_as_float(r[4 * i + 0]);
+                            f.y = __uint_as_float(r[4 * i + 1]);
+                            f.z = __uint_as_float(r[4 * i + 2]);
+                            f.w = __uint_as_float(r[4 * i + 3]);
+                            *reinterpret_cast<float4*>(orow + c0 + 4 * i) = f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (c0 + i < g.C) orow[c0 + i] = __uint_as_float(r[i]);
+                    }
+                }
+            }
             if (have && ok) {
-                uint32_t r2[16];
-                const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(ch * 16);
-                tmem_ld16(ta, r);
-                tmem_ld16(ta + TN, r2);
-                if (F16) {
-                    // lead + 2^-11 corrections, then undo the row and column scales
-                    const float rsi = row_ok ? g.rs_inv[pr.rs_off + row] : 0.f;
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float csi = csi_s[ch * 16 + i];
-                        r[i] = __float_as_uint(
-                            (__uint_as_float(r[i]) + __uint_as_float(r2[i]) * (1.f / 2048.f)) *
-                            rsi * csi);
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        r[i] = __float_as_uint(__uint_as_float(r[i]) + __uint_as_float(r2[i]));
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) r[i] = 0u;
+                // the accumulator is free for the next tile's MMAs
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(acc_empty);
+                ++nacc;
             }
-            const int c0 = cbase + ch * 16;
-            if (!row_ok || c0 >= g.C) continue;
-            if (vec && c0 + 16 <= g.C) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float4 f;
-                    f.x = __uint_as_float(r[4 * i + 0]);
-                    f.y = __uint_as_float(r[4 * i + 1]);
-                    f.z = __uint_as_float(r[4 * i + 2]);
-                    f.w = __uint_as_float(r[4 * i + 3]);
-                    *reinterpret_cast<float4*>(orow + c0 + 4 * i) = f;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c0 + i < g.C) orow[c0 + i] = __uint_as_float(r[i]);
-            }
-        }
         }
     }
-    if (*abort_flag && threadIdx.x == 0 && g.status) atomicOr(g.status, 1);
+    if (*abort_flag && threadIdx.x == 0) args.mark_timeout();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        // MMAs still in flight after an abort must finish before the
-        // accumulator is released (bounded as well).
-        if (*abort_flag && nst > 0) {
-            const long long t0 = clock64();
-            while (!mbar_try(done, 0) && clock64() - t0 < kWaitCycles) {
-            }
+        // every MMA has completed before the accumulator is released
+        // (bounded as well)
+        const long long t0 = clock64();
+        while (!mbar_try(fin, 0) && clock64() - t0 < kWaitCycles) {
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -746,12 +833,13 @@ __device__ __forceinline__ void split_gemm_body(const GemmArgs& g, const int4 ti
 template <int T, bool F16, bool BPRE, int TN>
 __global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
     split_gemm_kernel(const __grid_constant__ GemmArgs g) {
-    split_gemm_body<T, F16, BPRE, TN>(g, g.tiles[blockIdx.x]);
+    split_gemm_body<T, F16, BPRE, TN>(OnePlanArgs{g}, g.tiles, g.ntiles);
 }
 
 // Grouped launch: tile.w is the plan's index in the group.
 struct GemmGroup {
     int n;
+    int ntiles;
     GemmArgs a[kMaxGroup];
     const int4* tiles;
 };
@@ -759,8 +847,7 @@ struct GemmGroup {
 template <int T, bool F16, bool BPRE, int TN>
 __global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
     split_gemm_group_kernel(const __grid_constant__ GemmGroup G) {
-    const int4 t = G.tiles[blockIdx.x];
-    split_gemm_body<T, F16, BPRE, TN>(G.a[t.w], t);
+    split_gemm_body<T, F16, BPRE, TN>(GroupPlanArgs{G.a, G.n}, G.tiles, G.ntiles);
 }
 
 // Split the FP32 operand B of every inverse problem (the spectrum rows of
@@ -1102,6 +1189,7 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.plane_bytes = (long long)(inverse ? st->inv_plane_bytes : st->fwd_plane_bytes);
     g.probs = inverse ? st->d_probs_inv : st->d_probs_fwd;
     g.tiles = inverse ? st->d_tiles_inv : st->d_tiles_fwd;
+    g.ntiles = inverse ? st->ntiles_inv : st->ntiles_fwd;
     g.B = static_cast<const float*>(B);
     g.O = static_cast<float*>(O);
     g.C = 2 * p->F;
@@ -1122,12 +1210,45 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     return g;
 }
 
+// Persistent grid: as many CTAs as are resident on the device at once (the
+// per-SM count the shared memory and tensor memory are sized for), at most
+// one per tile.
+int persistent_ctas(int per_sm, int ntiles) {
+    static std::mutex mu;
+    static std::map<int, int> sms_of;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = sms_of.find(dev);
+        if (it != sms_of.end()) sms = it->second;
+    }
+    if (sms == 0) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        sms_of[dev] = sms;
+    }
+    return std::max(1, std::min(ntiles, sms * per_sm));
+}
+
 template <int T, bool F16, bool BPRE, int TN>
 cudaError_t gemm_launch(const GemmArgs& g, int ntiles, cudaStream_t s) {
     constexpr int smem = Cfg<T, BPRE, TN>::SMEM;
-    cudaError_t e = ensure_smem((const void*)split_gemm_kernel<T, F16, BPRE, TN>, smem);
+    const void* fn = (const void*)split_gemm_kernel<T, F16, BPRE, TN>;
+    cudaError_t e = ensure_smem(fn, smem);
     if (e) return e;
-    split_gemm_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(g);
+    // inverse (short tiles, K <= N / 2 + 1): persistent CTAs, so that the
+    // next tile's operands load during the last one's epilogue; forward (41
+    // K steps per tile at T639): one CTA per tile, which the hardware
+    // schedules in list order, so that the column tiles sharing a P~ tile
+    // run together and that tile comes from L2 after its first read
+    const int nctas = BPRE ? persistent_ctas(Wid<TN>::CTAS_PER_SM, ntiles) : ntiles;
+    split_gemm_kernel<T, F16, BPRE, TN><<<nctas, NTHREADS, smem, s>>>(g);
     note_launch();
     return cudaGetLastError();
 }
@@ -1428,9 +1549,16 @@ void split_group_tiles(sht_plan_s* const* plans, int n, bool inverse, std::vecto
 template <int T, bool F16, bool BPRE, int TN>
 cudaError_t group_launch(const GemmGroup& G, int ntiles, cudaStream_t s) {
     constexpr int smem = Cfg<T, BPRE, TN>::SMEM;
-    cudaError_t e = ensure_smem((const void*)split_gemm_group_kernel<T, F16, BPRE, TN>, smem);
+    const void* fn = (const void*)split_gemm_group_kernel<T, F16, BPRE, TN>;
+    cudaError_t e = ensure_smem(fn, smem);
     if (e) return e;
-    split_gemm_group_kernel<T, F16, BPRE, TN><<<ntiles, NTHREADS, smem, s>>>(G);
+    // inverse (short tiles, K <= N / 2 + 1): persistent CTAs, so that the
+    // next tile's operands load during the last one's epilogue; forward (41
+    // K steps per tile at T639): one CTA per tile, which the hardware
+    // schedules in list order, so that the column tiles sharing a P~ tile
+    // run together and that tile comes from L2 after its first read
+    const int nctas = BPRE ? persistent_ctas(Wid<TN>::CTAS_PER_SM, ntiles) : ntiles;
+    split_gemm_group_kernel<T, F16, BPRE, TN><<<nctas, NTHREADS, smem, s>>>(G);
     note_launch();
     return cudaGetLastError();
 }
@@ -1440,6 +1568,7 @@ cudaError_t launch_split_group(sht_plan_s* const* plans, int n, bool inverse,
                                int ntiles, cudaStream_t s) {
     GemmGroup G;
     G.n = n;
+    G.ntiles = ntiles;
     G.tiles = tiles;
     for (int q = 0; q < n; ++q) G.a[q] = make_gemm_args(plans[q], inverse, in[q], out[q]);
     const SplitTables* st = plans[0]->split;
