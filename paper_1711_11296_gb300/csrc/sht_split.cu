@@ -854,15 +854,18 @@ __global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
 // one (m, parity)) into T 16-bit terms, stored as pre-tiled K-major B tiles
 // (the layout the converters build in shared memory): tile (problem,
 // k-tile it, column tile ct) at bt_off + (it nct + ct) * B_TILE_BYTES of
-// each term plane.  Block (problem, 32 columns); lane = column, warp w
-// takes the groups of 8 K rows g = w, w + 8, ... (reads coalesced over the
-// columns, 16 bytes written per term and group).  FP16 scales each column
-// as the GEMM's converters do.
+// each term plane.  Block (problem, 128 columns); warp w keeps 32 columns
+// (lane = column of group w % 4) and takes the groups of 8 K rows
+// g = w / 4, w / 4 + 2, ... (reads coalesced over the columns, 16 bytes
+// written per term and group).  FP16 scales each column as the GEMM's
+// converters do.
 // The same pass computes the Equator row of the problem's output,
 // sum_r P~_{n_r}^m(0) X_{n_r}[c] (Eq. iLT at mu = 0), which the GEMM tiles
 // leave out: a compensated FP32 dot product (P~ as a float pair hi + lo,
 // exact products by FMA, two-sum accumulation) of the unscaled FP32
-// inputs, the 8 warps' partial sums combined in a fixed order.
+// inputs, the two warps' partial sums of a column combined in a fixed
+// order.  For the odd parity (n - m odd) P~(0) vanishes and the Equator
+// value is 0.
 __device__ __forceinline__ void two_sum_acc(float& h, float& l, float a, float al) {
     const float sum = __fadd_rn(h, a);
     const float bp = __fsub_rn(sum, h);
@@ -882,20 +885,23 @@ __global__ void __launch_bounds__(256)
     __shared__ float2 red[8][32];
     const int p = blockIdx.x;
     const SplitProb pr = probs[p];
+    const bool even = (p & 1) == 0;
     const size_t row0 = coef_offset(N, p >> 1) + (p & 1);
-    for (int k = threadIdx.x; k < pr.K; k += blockDim.x) {
-        const double v = pnm[(row0 + 2 * (size_t)k) * ldp + (Jh - 1)];
-        const float hi = (float)v;
-        peq[k] = make_float2(hi, (float)(v - (double)hi));
+    if (even) {
+        for (int k = threadIdx.x; k < pr.K; k += blockDim.x) {
+            const double v = pnm[(row0 + 2 * (size_t)k) * ldp + (Jh - 1)];
+            const float hi = (float)v;
+            peq[k] = make_float2(hi, (float)(v - (double)hi));
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c = blockIdx.y * 32 + lane;
+    const int c = blockIdx.y * 128 + (w & 3) * 32 + lane;
     const bool cin = c < C;
     const float cs = (F16 && cin) ? col_scale(colmax[c]) : 1.f;
     const int ct = c / TN, cc = c % TN;
     float eh = 0.f, el = 0.f;
-    for (int g = w; g < pr.nkt * (TK / 8); g += 8) {
+    for (int g = w >> 2; g < pr.nkt * (TK / 8); g += 2) {
         const int it = g / (TK / 8), k8 = g % (TK / 8);
         float x[8];
 #pragma unroll
@@ -904,13 +910,15 @@ __global__ void __launch_bounds__(256)
             x[e] = (k < pr.K && cin) ? __ldg(B + pr.b_off + (long long)k * pr.b_stride + c)
                                      : 0.f;
         }
+        if (even) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int k = g * 8 + e;
-            if (k < pr.K) {
-                const float2 pe = peq[k];
-                const float ph = __fmul_rn(pe.x, x[e]);
-                two_sum_acc(eh, el, ph, fmaf(pe.y, x[e], fmaf(pe.x, x[e], -ph)));
+            for (int e = 0; e < 8; ++e) {
+                const int k = g * 8 + e;
+                if (k < pr.K) {
+                    const float2 pe = peq[k];
+                    const float ph = __fmul_rn(pe.x, x[e]);
+                    two_sum_acc(eh, el, ph, fmaf(pe.y, x[e], fmaf(pe.x, x[e], -ph)));
+                }
             }
         }
         if (F16) {
@@ -926,17 +934,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) x[e] *= 2048.f;
             }
-            *reinterpret_cast<uint4*>(planes + (long long)t * plane_bytes + off) = pk;
+            // columns past C inside the last tile are written as zero;
+            // those past the tiles (64-wide tiles) are not stored
+            if (ct < nct) *reinterpret_cast<uint4*>(planes + (long long)t * plane_bytes + off) = pk;
         }
     }
     red[w][lane] = make_float2(eh, el);
     __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int v = 1; v < 8; ++v) {
-            const float2 r = red[v][lane];
-            two_sum_acc(eh, el, r.x, r.y);
-        }
+    if (w < 4) {
+        const float2 r = red[w + 4][lane];
+        two_sum_acc(eh, el, r.x, r.y);
         if (cin) O[pr.o_off + (long long)pr.Mrows * pr.o_stride + c] = __fadd_rn(eh, el);
     }
 }
@@ -1279,7 +1286,7 @@ cudaError_t launch_split_b_inverse(const sht_plan_s* p, const void* spec, void* 
     const int C = 2 * p->F, nct = (C + st->tn - 1) / st->tn;
     cudaError_t e;
     if (st->fp16 && (e = launch_colmax_inverse(p, spec, s))) return e;
-    const dim3 grid(2 * (p->N + 1), nct * (st->tn / 32));
+    const dim3 grid(2 * (p->N + 1), (C + 127) / 128);
     const size_t smem = (size_t)std::max(st->inv_max_nkt, 1) * TK * sizeof(float2);
     const float* B = static_cast<const float*>(spec);
     float* O = static_cast<float*>(work);
