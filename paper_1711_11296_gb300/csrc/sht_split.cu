@@ -641,38 +641,46 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
                 const int cg = cbase + tid % TN;
                 if (cg < g.C) cs = col_scale(g.colmax[cg]);
             }
-            for (int li = 0; li < (BPRE ? 0 : nst); ++li, ++qb) {
-                const int it = kb + li;
-                const int sb = qb % NBB, r = qr % NRS;
-                // B-term slot sb is free once the MMAs of its previous use
-                // are done; the FP32 rows wait in raw slot r
-                // (a lane that gives up leaves alone; the warp agrees on ok
-                // again before the epilogue's collective operations)
-                if (!(ok = mbar_wait(empty_b(sb), ((qb / NBB) & 1u) ^ 1u, abort_flag))) break;
-                if (g.raw_bulk && !(ok = mbar_wait(full_r(r), (qr / NRS) & 1u, abort_flag)))
-                    break;
-                const float* raw =
-                    reinterpret_cast<const float*>(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
+            // Thread tid converts column c, K rows k8 * 8 .. + 7 of each
+            // stage (threads past TN * TK / 8 only take part in the
+            // barriers).  Software-pipelined over two register buffers: the
+            // next stage's values are read (and their raw slot released)
+            // before this stage's terms are formed and stored.
+            static_assert(TN * TK / 8 <= NCONV, "one 8-value unit per thread and stage");
+            const bool unit = tid < TN * TK / 8;
+            const int c = tid % TN, k8 = tid / TN, cg = cbase + c;
+            const bool cin = unit && cg < g.C;
+            const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
+            // the 8 values of stage li into x (false: the wait gave up)
+            auto fetch = [&](int li, float (&x)[8]) -> bool {
+                const int k = (kb + li) * TK + k8 * 8;
+                if (g.raw_bulk) {
+                    const uint32_t q = qr + (uint32_t)li;
+                    const int r = q % NRS;
+                    if (!mbar_wait(full_r(r), (q / NRS) & 1u, abort_flag)) return false;
+                    const float* raw = reinterpret_cast<const float*>(
+                        smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        x[e] = (cin && k + e < pr.K) ? raw[(k8 * 8 + e) * TN + c] : 0.f;
+                    mbar_arrive(empty_r(r));
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        x[e] = (cin && k + e < pr.K)
+                                   ? __ldg(g.B + pr.b_off + (long long)(k + e) * pr.b_stride + cg)
+                                   : 0.f;
+                }
+                return true;
+            };
+            // B-term slot of stage li free (the MMAs of its previous use are
+            // done), then the T terms of x stored into it
+            auto convert = [&](int li, float (&x)[8]) -> bool {
+                const uint32_t qq = qb + (uint32_t)li;
+                const int sb = qq % NBB;
+                if (!mbar_wait(empty_b(sb), ((qq / NBB) & 1u) ^ 1u, abort_flag)) return false;
                 unsigned char* bst = smem + CF::B_OFF + sb * CF::B_SLOT;
-                const int k0 = it * TK;
-#pragma unroll
-                for (int u = tid; u < TN * TK / 8; u += NCONV) {
-                    const int c = u % TN;
-                    const int k8 = u / TN;
-                    const int cg = cbase + c;
-                    float x[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int kk = k8 * 8 + e;
-                        const bool in = (k0 + kk < pr.K) && (cg < g.C);
-                        if (g.raw_bulk)
-                            x[e] = in ? raw[kk * TN + c] : 0.f;
-                        else
-                            x[e] = in ? __ldg(g.B + pr.b_off + (long long)(k0 + kk) * pr.b_stride +
-                                              cg)
-                                      : 0.f;
-                    }
-                    const int off = ((c >> 3) * (TK / 8) + k8) * 128 + (c & 7) * 16;
+                if (unit) {
                     if (F16) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) x[e] *= cs;
@@ -690,10 +698,30 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(full_b(sb));
-                if (g.raw_bulk) {
-                    mbar_arrive(empty_r(r));
-                    ++qr;
+                return true;
+            };
+            // (a lane that gives up leaves alone; the warp agrees on ok
+            // again before the epilogue's collective operations)
+            const int ncv = BPRE ? 0 : nst;
+            float xa[8];
+            if constexpr (TN == 128) {
+                float xb[8];
+                if (ncv > 0) ok = fetch(0, xa);
+                for (int li = 0; li < ncv && ok; li += 2) {
+                    if (li + 1 < ncv && !(ok = fetch(li + 1, xb))) break;
+                    if (!(ok = convert(li, xa))) break;
+                    if (li + 1 >= ncv) break;
+                    if (li + 2 < ncv && !(ok = fetch(li + 2, xa))) break;
+                    if (!(ok = convert(li + 1, xb))) break;
                 }
+            } else {
+                // three CTAs per SM leave 56 registers a thread: one buffer
+                for (int li = 0; li < ncv && ok; ++li)
+                    ok = fetch(li, xa) && convert(li, xa);
+            }
+            if (!BPRE) {
+                qb += (uint32_t)ncv;
+                if (g.raw_bulk) qr += (uint32_t)ncv;
             }
             // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (the
             // tile rows it may access) for column half w / 4 ----
