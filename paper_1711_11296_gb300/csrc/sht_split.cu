@@ -9,7 +9,8 @@
 // where c runs over the 2F real columns.  Operands are split into T = 2 or
 // 3 BF16 terms, x = x_1 + x_2 (+ x_3), x_{t+1} = bf16(x - x_1 - .. - x_t),
 // and the products x_a y_b with a + b <= T - 1 (0-based) are accumulated in
-// one FP32 accumulator in tensor memory (3 products for T = 2, 6 for T = 3).
+// FP32 in tensor memory (3 products for T = 2, 6 for T = 3): the leading
+// product x_1 y_1 in one accumulator, the corrections in a second.
 //
 // A (the P~ table) is split once at plan time and stored pre-tiled in the
 // canonical no-swizzle K-major layout of the tensor-core shared-memory
@@ -21,19 +22,22 @@
 // block of a tile arrives as one tiled tensor copy (cp.async.bulk.tensor
 // over the whole Fourier workspace viewed as a row-major matrix of 2F
 // columns) when the rows are 16-byte aligned (even field counts), else by
-// one bulk copy per row, else the converters load it directly.  A bulk
-// copy costs about the same SM time whatever its size, so one copy per
-// stage instead of TK keeps the copy engine from bounding the pipeline.
-// The converter warps split B into BF16 terms, stored in the same K-major
-// core-matrix layout.
+// one bulk copy per row, else the converters load it directly.  (Sixteen
+// 512-byte row copies per stage kept the copy warp issuing for most of a
+// stage; one tiled copy does not.)  The converter warps split B into BF16
+// terms, stored in the same K-major core-matrix layout, reading the next
+// stage's values before they split this stage's.
 //
-// One CTA computes a 128 x 128 output tile through a 3-stage pipeline
-// (two CTAs share an SM, so one's prologue and epilogue overlap the
-// other's main loop):
-// warps 0-7 convert B and run the epilogue (tcgen05.ld of the 32 TMEM lanes
-// a warp may access, for half of the columns each), warp 8 issues the bulk
-// copies, one thread of warp 9 issues tcgen05.mma (M = 128, N = 128,
-// K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
+// A CTA computes 128 x TN output tiles through rings of mbarrier stages
+// (the A tiles, the FP32 B rows and the converted B terms each in a ring of
+// its own; two CTAs share an SM, so one's prologue and epilogue overlap the
+// other's main loop): the forward launches one CTA per tile, the inverse
+// persistent CTAs that stride over the tile list.  Warps 0-7 convert B and
+// run the epilogue (tcgen05.ld of the 32 TMEM lanes a warp may access, for
+// half of the columns each), warp 8 issues the bulk copies of A (and of the
+// pre-split inverse B), warp 10 those of the forward's FP32 B, one thread
+// of warp 9 issues tcgen05.mma (M = 128, N = TN or, transposed, N = the
+// tile's rows; K = 16) and commits to mbarriers.  Every wait is bounded by a clock limit;
 // a CTA that gives up records SHT_ERR_TIMEOUT in the plan's status word,
 // waits (bounded) for its MMAs and frees its tensor memory.
 #include <cuda.h>
