@@ -21,8 +21,8 @@
 // B (the FP32 Fourier data or spectrum) stays FP32 in HBM.  The TK x TN
 // block of a tile arrives as one tiled tensor copy (cp.async.bulk.tensor
 // over the whole Fourier workspace viewed as a row-major matrix of 2F
-// columns) when the rows are 16-byte aligned (even field counts), else by
-// one bulk copy per row, else the converters load it directly.  (Sixteen
+// columns) when the rows are 16-byte aligned (even field counts), else the
+// converters load it directly.  (Sixteen
 // 512-byte row copies per stage kept the copy warp issuing for most of a
 // stage; one tiled copy does not.)  The converter warps split B into BF16
 // terms, stored in the same K-major core-matrix layout, reading the next
@@ -154,8 +154,8 @@ struct GemmArgs {
     const float* B;
     float* O;
     int C;                          // valid columns (2F)
-    int raw_bulk;                   // 1: B rows arrive by bulk copy (16-byte aligned),
-                                    // 2: as one tiled tensor copy per stage (bmap)
+    int raw_bulk;                   // 1: B's rows arrive as one tiled tensor copy per
+                                    // stage (bmap); 0: the converters load them
     int* status;
     const float* rs_inv;            // FP16: 1 / row scale per A row (pr.rs_off + row)
     const unsigned* colmax;         // FP16: max |B| per column (float bits)
@@ -163,7 +163,7 @@ struct GemmArgs {
     long long bplane_bytes;
     int nct;                        // column tiles (pre-split B tile index = it * nct + ct)
     int stall;                      // fault injection for tests: CTA 0 never arms stage 0
-    // raw_bulk == 2: B as a row-major matrix [rows][C] of floats (problem
+    // raw_bulk: B as a row-major matrix [rows][C] of floats (problem
     // rows at b_off / b_stride), box TN columns x TK rows; out-of-range
     // columns and rows read as zero
     CUtensorMap bmap;
@@ -500,8 +500,7 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
         }
     } else if (warp == WARP_RAW) {
         // ---- the FP32 rows of B into the raw ring, NR stages ahead of the
-        // converters: one tiled tensor copy per stage, or one bulk copy per
-        // row (lane k copies row k) ----
+        // converters: one tiled tensor copy per stage ----
         uint32_t q = 0, issued = 0;   // raw stages passed / issued in this CTA
         bool ok = true;
         for (int tt = blockIdx.x; !BPRE && tt < ntiles && ok && !aborted(); tt += gridDim.x) {
@@ -511,10 +510,7 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
             const SplitProb pr = g.probs[tile.x];
             const int mt = tile.y, ct = tile.z, kb = pr.kt0, nst = stages(pr, mt);
             const int cbase = ct * TN;
-            const int ccopy = min(TN, g.C - cbase);   // valid columns
-            const uint32_t rbytes = (uint32_t)ccopy * 4u;
-            const bool tiled = g.raw_bulk == 2;
-            const int y0 = tiled ? (int)(pr.b_off / pr.b_stride) : 0;   // matrix row of k = 0
+            const int y0 = (int)(pr.b_off / pr.b_stride);   // matrix row of k = 0
             for (int li = 0; li < nst; ++li, ++q) {
                 const int it = kb + li;
                 const int r = q % NRS;
@@ -525,27 +521,16 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
                 issued = q + 1;
                 const int k0 = it * TK;
                 const uint32_t dst = smem_u32(smem + CF::RAW_OFF + r * Wid<TN>::RAW_BYTES);
-                if (tiled) {
-                    // the whole box lands (rows past K belong to the next
-                    // problem or read as zero; the converters skip them)
-                    if (lane == 0) {
-                        mbar_expect_tx(full_r(r), (uint32_t)(TK * TN * 4));
-                        tensor_g2s_2d(dst, &g.bmap, cbase, y0 + k0, full_r(r));
-                    }
-                    __syncwarp();
-                    continue;
+                // the whole box lands (rows past K belong to the next problem
+                // or read as zero; the converters skip them)
+                if (lane == 0) {
+                    mbar_expect_tx(full_r(r), (uint32_t)(TK * TN * 4));
+                    tensor_g2s_2d(dst, &g.bmap, cbase, y0 + k0, full_r(r));
                 }
-                const int krows = max(0, min(TK, pr.K - k0));
-                if (lane == 0) mbar_expect_tx(full_r(r), rbytes * (uint32_t)krows);
-                __syncwarp();
-                if (lane < krows)
-                    bulk_g2s(dst + lane * TN * 4,
-                             g.B + pr.b_off + (long long)(k0 + lane) * pr.b_stride + cbase,
-                             rbytes, full_r(r));
                 __syncwarp();
             }
         }
-        // after an abort, let the row copies already issued land (bounded)
+        // after an abort, let the copies already issued land (bounded)
         if (lane == 0 && *abort_flag) {
             for (uint32_t j = issued > (uint32_t)NRS ? issued - NRS : 0u; j < issued; ++j) {
                 const long long t0 = clock64();
@@ -1232,8 +1217,7 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.B = static_cast<const float*>(B);
     g.O = static_cast<float*>(O);
     g.C = 2 * p->F;
-    // rows of B are 16-byte aligned when C is a multiple of 4 floats
-    g.raw_bulk = ((g.C & 3) == 0) && (((uintptr_t)B & 15) == 0) ? 1 : 0;
+    g.raw_bulk = 0;
     g.status = p->d_status;
     g.rs_inv = inverse ? st->rs_inv : st->rs_fwd;
     g.colmax = p->d_colmax ? p->d_colmax + (inverse ? g.C : 0) : nullptr;
@@ -1242,10 +1226,11 @@ GemmArgs make_gemm_args(const sht_plan_s* p, bool inverse, const void* B, void* 
     g.stall = (!inverse && st->inject_stall) ? 1 : 0;
     g.bplane_bytes = inverse ? (long long)st->inv_bplane_bytes : 0;
     // forward B: the Fourier workspace, problem (m, parity) at rows
-    // (2 m + parity) Jh .. + Jh - 1 of a [2 (N + 1) Jh][C] matrix
-    if (!inverse && g.raw_bulk &&
+    // (2 m + parity) Jh .. + Jh - 1 of a [2 (N + 1) Jh][C] matrix; tiled
+    // copies need 16-byte aligned rows (C a multiple of 4 floats)
+    if (!inverse && (g.C & 3) == 0 && ((uintptr_t)B & 15) == 0 &&
         encode_b_map(&g.bmap, B, g.C, 2LL * (p->N + 1) * p->Jh, st->tn))
-        g.raw_bulk = 2;
+        g.raw_bulk = 1;
     return g;
 }
 
