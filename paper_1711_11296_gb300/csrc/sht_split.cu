@@ -357,8 +357,9 @@ struct GroupPlanArgs {
     }
 };
 
-// Persistent CTAs: CTA b computes tiles b, b + gridDim.x, ... of the list.
-// The rings and their phases run on across tiles (every role walks the
+// CTA b computes tiles b, b + gridDim.x, ... of the list (one tile when the
+// grid has a CTA per tile; many for the persistent inverse grid).  The
+// rings and their phases run on across tiles (every role walks the
 // same tiles and stages, so its running stage count names the slot and
 // phase), the copy warps prefetch the next tile's operands while the
 // converter warps drain the accumulator of the last one, and the MMA warp
