@@ -246,6 +246,14 @@ __device__ __forceinline__ void tensor_g2s_2d(uint32_t dst, const CUtensorMap* m
         : "memory");
 }
 
+// The same box fetched into L2 only (no shared memory, no barrier).
+__device__ __forceinline__ void tensor_prefetch_l2_2d(const CUtensorMap* map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor, no swizzle: start address, leading
 // (K-direction core stride) and stride (M/N-direction 8-row-group stride)
 // byte offsets, descriptor version 1 at bit 46.
@@ -502,6 +510,7 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
     } else if (warp == WARP_RAW) {
         // ---- the FP32 rows of B into the raw ring, NR stages ahead of the
         // converters: one tiled tensor copy per stage ----
+        constexpr int PF_L2 = 4;   // L2 prefetch distance beyond the copy, in stages
         uint32_t q = 0, issued = 0;   // raw stages passed / issued in this CTA
         bool ok = true;
         for (int tt = blockIdx.x; !BPRE && tt < ntiles && ok && !aborted(); tt += gridDim.x) {
@@ -527,6 +536,10 @@ __device__ __forceinline__ void split_gemm_body(const Args& args, const int4* __
                 if (lane == 0) {
                     mbar_expect_tx(full_r(r), (uint32_t)(TK * TN * 4));
                     tensor_g2s_2d(dst, &g.bmap, cbase, y0 + k0, full_r(r));
+                    // the rows of a later stage into L2, so that its copy
+                    // into the ring comes from L2 rather than HBM
+                    if (li + PF_L2 < nst)
+                        tensor_prefetch_l2_2d(&g.bmap, cbase, y0 + k0 + PF_L2 * TK);
                 }
                 __syncwarp();
             }
