@@ -196,7 +196,7 @@ def fft_bytes(w, F, real_bytes, npts=None):
 # when a launch ends are not counted by the capture.  Keyed by (stage, path,
 # workload, field-levels); an entry is removed whenever its kernel changes
 # and re-added from a new capture.
-_FFT_INV_T639x64 = (419.898 + 786.317) * 1e6   # bytes, fft_inverse<float, 1280>
+_FFT_INV_T639x64 = (419.963 + 786.312) * 1e6   # bytes, fft_inverse<float, 1280>
 MEASURED_TRAFFIC = {}
 for _p in ("bf16x3", "bf16x2", "fp16x3", "fp16x2"):   # the same FP32 inverse FFT
     MEASURED_TRAFFIC[("fft_inverse", _p, "T639", 256)] = _FFT_INV_T639x64 * 256 / 64
