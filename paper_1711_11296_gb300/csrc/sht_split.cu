@@ -874,6 +874,8 @@ struct GemmGroup {
     GemmArgs a[kMaxGroup];
     const int4* tiles;
 };
+// passed by value as a kernel parameter (each GemmArgs holds a tensor map)
+static_assert(sizeof(GemmGroup) <= 4096, "grouped GEMM arguments fit the 4 KB parameter space");
 
 template <int T, bool F16, bool BPRE, int TN>
 __global__ void __launch_bounds__(NTHREADS, Wid<TN>::CTAS_PER_SM)
